@@ -1,0 +1,149 @@
+"""Pins for the oracle's TWA sampling and ensemble moments (Sec. III.A-III.C).
+
+Checked against: the coherent-state Wigner function's exact moments, the
+exactness of the TWA for a quadratic Hamiltonian (free field), the paper's
+n_s Q_s invariance (Eq. Q_relation), brute-force Fock-space evolution of a
+3-site lattice (the exact quantum answer), and the single-mode Kerr oscillator
+of Fig. 2 in closed form.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import twa_inputs as ti
+from oracle import fock, kerr, sp, twa
+
+
+def _bump(m=64):
+    g = ti.Grid.cube(1, m)
+    return g, ti.cosine_overdensity(g, 0.5)
+
+
+def test_sample_slot0_is_classical_and_noise_variance():
+    g, psi = _bump()
+    n, Ns = 1e4, 400
+    b = twa.sample(psi, 3, Ns, n, g.dV)
+    assert np.array_equal(b[0], psi)
+    d = (b[1:] - psi[None]).ravel()
+    sig2 = 1.0 / (4.0 * n * g.dV)                    # complex variance 1/2 per mode
+    for comp in (d.real, d.imag):
+        assert abs(comp.var() / sig2 - 1.0) < 5 * math.sqrt(2.0 / comp.size)
+    lit = twa.sample(psi, 3, Ns, n, g.dV, noise_conv=1)
+    assert np.allclose((lit[1:] - psi).var(), 2.0 * (b[1:] - psi).var(), rtol=1e-12)
+
+
+def test_noise_is_white_with_half_quantum_per_mode():
+    g, psi = _bump(32)
+    n, Ns = 1e6, 2000
+    b = twa.sample(psi, 11, Ns, n, g.dV)
+    da = np.fft.fft(b[1:] - psi, axis=-1) * math.sqrt(n * g.dV / g.cells)
+    e = (np.abs(da) ** 2).mean(axis=0)                 # E |delta a_k|^2 per mode
+    assert np.all(np.abs(e - 0.5) < 5 * 0.5 / math.sqrt(Ns))
+
+
+def test_moments_of_the_initial_coherent_state():
+    g, psi = _bump(32)
+    n, Ns = 50.0, 20000
+    b = twa.sample(psi, 5, Ns, n, g.dV)
+    m = twa.moments(b, n, 1.0, 1)
+    z2 = np.abs(np.fft.fft(psi) * math.sqrt(n * g.dV / g.cells)) ** 2
+    # a coherent state has <n_k> = |z_k|^2 and Var n_k = |z_k|^2 (Poisson)
+    se = np.sqrt((z2 + 0.25) / Ns)
+    assert np.all(np.abs(m["nk_mean"] - z2) < 5 * se)
+    se_var = np.sqrt((2 * z2 ** 2 + 4 * z2 + 1) / Ns) + 1e-3
+    assert np.all(np.abs(m["nk_var"] - z2) < 6 * se_var)
+    # Q(0): a coherent state has Q = 0; the sample estimator's bias is -M/(2 n N_s)
+    M = g.cells
+    assert abs(m["Q"] + M / (2 * n * Ns)) < 6 * (M / (2 * n)) / math.sqrt(M * Ns)
+    assert np.allclose(m["rho_cl"], np.abs(psi) ** 2)
+    assert abs(np.sum(m["rho_mean"]) * g.dV - 1.0) < 5e-3
+
+
+def test_free_field_twa_is_exact():
+    # quadratic H: every |a_k|^2 is conserved stream by stream, and so is Q
+    g, psi = _bump(64)
+    n = 1e3
+    t, series, _ = twa.run(psi, 0.05, 0.0, 0.01, 1.0, 1, n, 16, 9, 30, 10)
+    for s in series[1:]:
+        assert np.max(np.abs(s["nk_mean"] - series[0]["nk_mean"])) < 1e-9
+        assert abs(s["Q"] - series[0]["Q"]) < 1e-12
+
+
+def test_nsQs_is_independent_of_the_sampling_n():
+    # Eq. Q_relation: with the same normals, n_s Q_s agrees across n_s while Q << 1
+    g, psi = _bump(64)
+    out = []
+    for n in (1e8, 1e10):
+        t, series, _ = twa.run(psi, 0.01, 4 * np.pi, 2e-3, 1.0, 1, n, 32, 21, 150, 50,
+                               with_modes=False)
+        q = np.array([s["Q"] for s in series])
+        out.append(n * (q - q[0]))
+    assert np.all(np.abs(out[0][1:] - out[1][1:]) < 0.02 * np.abs(out[1][1:]) + 1e-9)
+    assert out[1][-1] > 0
+
+
+def _fock_case(M, C=200.0, amp=0.9, n=10.0, times=(0.0, 0.02, 0.05)):
+    x = np.arange(M) / M
+    psi = np.sqrt(1 + amp * np.cos(2 * np.pi * x)).astype(complex)
+    psi /= np.sqrt(np.sum(np.abs(psi) ** 2) / M)
+    return psi, C, n, np.array(times)
+
+
+def _twa_nk(psi, C, n, times, Ns, noise_conv=0, dt=1e-3):
+    M = psi.size
+    cur = twa.sample(psi, 7, Ns, n, 1.0 / M, noise_conv)
+    res = []
+    s = 0
+    for t in times:
+        while s < int(round(t / dt)):
+            cur = sp.step(cur, 1.0, C, dt, 1.0, 1)
+            s += 1
+        a = np.fft.fft(cur, axis=-1) * math.sqrt(n * (1.0 / M) / M)
+        a2 = np.abs(a[1:]) ** 2
+        m2 = a2.mean(0)
+        var = (a2 ** 2).mean(0) - m2 - (m2 - 0.5) ** 2
+        infl = a2 ** 2 - a2 - 2 * (m2 - 0.5) * a2            # delta-method influence function
+        res.append((m2 - 0.5, a2.std(0) / math.sqrt(Ns), var, infl.std(0) / math.sqrt(Ns),
+                    np.abs(a[0]) ** 2))
+    return res
+
+
+@pytest.mark.parametrize("M", [2, 3])
+def test_twa_matches_brute_force_fock_evolution(M):
+    psi, C, n, times = _fock_case(M)
+    nk, var, prob = fock.mode_occupations(psi, 1.0, 1.0, C, n, times, n_max=40)
+    assert np.all(prob > 1 - 1e-9)
+    worst_cl = 0.0
+    for ti_, (m, se, v, sev, cl) in enumerate(_twa_nk(psi, C, n, times, 20000)):
+        assert np.all(np.abs(m - nk[ti_]) < 3.5 * se), (ti_, m, nk[ti_], se)
+        assert np.all(np.abs(v - var[ti_]) < 4.0 * sev), (ti_, v, var[ti_], sev)
+        worst_cl = max(worst_cl, float(np.max(np.abs(cl - nk[ti_]) / se)))
+    if M == 3:
+        # the classical (mean-field) trajectory misses the quantum correction by many sigma
+        assert worst_cl > 6.0
+
+
+def test_paper_literal_noise_reading_disagrees_with_fock():
+    psi, C, n, times = _fock_case(3, times=(0.0,))
+    nk, _, _ = fock.mode_occupations(psi, 1.0, 1.0, C, n, times, n_max=40)
+    m, se, _, _, _ = _twa_nk(psi, C, n, times, 20000, noise_conv=1)[0]
+    assert np.all(np.abs(m - nk[0]) > 8 * se)       # off by +1/2 per mode
+
+
+def test_kerr_ensemble_matches_closed_forms():
+    z, lam, Ns = math.sqrt(20.0), 1.0, 200000
+    # one "cell" with n dV = 1: psi is the mode amplitude itself
+    alpha0 = twa.sample(np.array([z + 0j]), 13, Ns, 1.0, 1.0)[1:, 0]
+    for th in (0.02, 0.05, 0.1):
+        mc = kerr.twa_trajectory(alpha0, lam, th).mean()
+        cf = kerr.twa_mean_closed_form(z, lam, th)
+        se = math.sqrt(0.5 / Ns) * 3
+        assert abs(mc - cf) < 4 * se
+        ex = kerr.exact_mean(z, lam, th)
+        mf = z * np.exp(-1j * lam * (abs(z) ** 2 - 1) * th)        # mean-field, no spread
+        assert abs(cf - ex) < 0.25 * abs(mf - ex)
+
+
+def test_q_physical_scaling():
+    assert twa.q_physical(1e-3, 1e8, 1e98) == pytest.approx(1e-93)
