@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Throughput of the batched FP32 TWA ensemble on one GB300 (and replicas on N GPUs).
+
+Workload: 3D Gaussian-random-field condensation (Sec. IV.B, Eq. kspaceGauss) on a
+128^3 periodic grid, 256 sampled streams plus the classical field, FP32 fields,
+kick-drift-kick steps at dt from the pi/4 kinetic rule, ensemble moments (FP64
+accumulation, per-mode occupations included) every 10 steps.  One bench step is
+one output interval: 10 KDK steps of the whole batch plus its moments, through
+the public call twa_advance on device-resident inputs.  Metric: TWA
+cell-updates/s = streams x cells x KDK steps / s (the classical field is
+evolved too but not counted).
+
+Also reported: the dominant pass's achieved HBM bandwidth (algorithmic bytes /
+CUDA-event time of its launches in the timed region) against the measured copy
+bandwidth; the FP64 CPU oracle on this host's cores (cpu_baseline); the plain
+FP64 single-realization GPU path and a cuFFT/torch reference step (context);
+end-to-end throughput of twa_run with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl twa|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TWA cell-updates/s, FP32 batched vs FP64 plain on 1 GB300, at stated err; %HBM peak"
+UNIT = "cell-updates/s"
+GRID_M = 128
+STREAMS = 256
+OUT_EVERY = 10
+SEED = 2024
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["twa", "reference"], default="twa")
+    ap.add_argument("--no-extras", action="store_true", help="skip cpu/f64/cufft/e2e side measurements")
+    return ap.parse_args()
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+def _workload():
+    import twa_inputs as ti
+    return ti.workload_3d_condensation(GRID_M, STREAMS, 2000)
+
+
+def _oracle_rate(w, n_fields=2, budget_s=12.0):
+    """FP64 oracle (scipy.fft on all host cores) on a bounded sample of the workload."""
+    import numpy as np
+    from oracle import sp, twa
+    cl = w.psi_cl()
+    b = twa.sample(cl, w.noise_seed, n_fields, w.phys.n_tot, w.grid.dV)[1:]
+    sp.step(b, w.phys.hbar_m, w.phys.C, w.phys.dt, 1.0, 3)          # warm the FFT plans
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        b = sp.step(b, w.phys.hbar_m, w.phys.C, w.phys.dt, 1.0, 3)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 50:
+            break
+    return n_fields * w.grid.cells * n / el, n, el
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands, timed on this host's cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import sp, twa
+    w = _workload()
+    cl = w.psi_cl()
+    nf = 2
+    b = twa.sample(cl, w.noise_seed, nf, w.phys.n_tot, w.grid.dV)[1:]
+    for _ in range(args.warmup):
+        b = sp.step(b, w.phys.hbar_m, w.phys.C, w.phys.dt, 1.0, 3)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b = sp.step(b, w.phys.hbar_m, w.phys.C, w.phys.dt, 1.0, 3)
+    el = time.perf_counter() - t0
+    val = nf * w.grid.cells * args.steps / el
+    sample = f"{nf} sampled streams of the 128^3 workload, 1 KDK step per bench step (FP64 numpy/scipy, workers={sp.WORKERS})"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3D Gaussian-random-field condensation 128^3 (oracle sample)", "streams": nf},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": _cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _f64_plain_rate(w, steps=2):
+    import torch
+    from paper_2310_07119_gb300 import Ensemble, F64_PLAIN
+    ens = Ensemble([w.grid], w.phys.hbar_m, w.phys.C, w.phys.dt, w.phys.n_tot, [1], precision=F64_PLAIN,
+                   want_modes=False)
+    ens.sample([w.psi_cl()], w.noise_seed)
+    ens.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ens.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ens.close()
+    fields = 2  # the plain path advances the classical field and the stream one after the other
+    return fields * w.grid.cells * steps / (ms * 1e-3)
+
+
+def _cufft_reference_rate(w, batch=32, steps=5):
+    """One KDK step written with torch.fft (cuFFT) and torch elementwise ops (timing reference only)."""
+    import torch
+    dev = torch.device("cuda")
+    m = w.grid.n[0]
+    k = 2 * math.pi * torch.fft.fftfreq(m, d=1.0 / m, dtype=torch.float64)
+    k2 = (k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2).to(dev)
+    kin = torch.exp(-1j * torch.remainder(w.phys.hbar_m * k2 * w.phys.dt / 2, 2 * math.pi)).to(torch.complex64)
+    inv = torch.where(k2 > 0, -w.phys.C / k2, torch.zeros_like(k2)).to(torch.float32)
+    psi = torch.randn((batch, m, m, m), dtype=torch.complex64, device=dev)
+    kick = w.phys.dt / (2 * w.phys.hbar_m)
+
+    def step(p):
+        V = torch.fft.ifftn(torch.fft.fftn(p.abs() ** 2, dim=(1, 2, 3)) * inv, dim=(1, 2, 3)).real
+        p = p * torch.exp(-1j * kick * V)
+        p = torch.fft.ifftn(torch.fft.fftn(p, dim=(1, 2, 3)) * kin, dim=(1, 2, 3))
+        V = torch.fft.ifftn(torch.fft.fftn(p.abs() ** 2, dim=(1, 2, 3)) * inv, dim=(1, 2, 3)).real
+        return p * torch.exp(-1j * kick * V)
+
+    psi = step(psi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        psi = step(psi)
+    e1.record()
+    torch.cuda.synchronize()
+    return batch * m ** 3 * steps / (e0.elapsed_time(e1) * 1e-3)
+
+
+def _e2e(ens, w, steps=2, n_run=50):
+    """twa_run from a pinned host psi_cl to the host series, copies inside the timed region."""
+    import torch
+    from paper_2310_07119_gb300 import twa_run
+    cl_host = torch.from_numpy(w.psi_cl().reshape(-1)).pin_memory()
+    cl_dev = torch.empty_like(cl_host, device=ens.device)
+    series = ens.new_series(n_run, OUT_EVERY)
+    series_host = torch.empty(series.shape, dtype=series.dtype).pin_memory()
+    st = torch.cuda.current_stream()
+    # warm-up (graph capture happens here)
+    cl_dev.copy_(cl_host, non_blocking=True)
+    twa_run(ens.h, cl_dev, SEED, n_run, OUT_EVERY, ens.psi, series)
+    series_host.copy_(series, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        cl_dev.copy_(cl_host, non_blocking=True)
+        twa_run(ens.h, cl_dev, SEED, n_run, OUT_EVERY, ens.psi, series)
+        series_host.copy_(series, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    val = STREAMS * w.grid.cells * n_run * steps / (ms * 1e-3)
+    return {"value": val, "unit": UNIT, "h2d_bytes_per_step": cl_host.numel() * cl_host.element_size(),
+            "d2h_bytes_per_step": series_host.numel() * series_host.element_size(),
+            "call": f"twa_run({n_run} KDK steps, moments every {OUT_EVERY}) incl. sampling, per step"}
+
+
+def run_twa(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2310_07119_gb300 import Ensemble, twa_advance, twa_last_launch_count, twa_profile_enable, twa_profile_read
+
+    w = _workload()
+    ens = Ensemble([w.grid], w.phys.hbar_m, w.phys.C, w.phys.dt, w.phys.n_tot, [STREAMS], want_modes=True,
+                   device=f"cuda:{local}")
+    cl = w.psi_cl()
+    ens.autotune(os.path.join(tempfile.gettempdir(), "twa_tune_cache.json"))
+    ens.sample([cl], w.noise_seed)
+    series_w = ens.new_series(max(1, args.warmup) * OUT_EVERY, OUT_EVERY)
+    twa_advance(ens.h, ens.psi, max(1, args.warmup) * OUT_EVERY, OUT_EVERY, series_w)
+    series = ens.new_series(args.steps * OUT_EVERY, OUT_EVERY)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    twa_profile_enable(ens.h, True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        twa_advance(ens.h, ens.psi, args.steps * OUT_EVERY, OUT_EVERY, series)
+        e1.record(st)
+        torch.cuda.synchronize()
+        launches = twa_last_launch_count(ens.h)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = twa_profile_read(ens.h)
+    twa_profile_enable(ens.h, False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cell_updates = STREAMS * w.grid.cells * OUT_EVERY * args.steps * world
+    value = cell_updates / (ms * 1e-3)
+    sc = series.cpu().numpy()
+
+    peak, peak_kind = _peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    name, d = dom
+    bytes_per_launch = d["bytes_per_cell"] * d["fields_per_launch"] * d["cells"]
+    avg_ms = d["total_ms"] / d["launches"]
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    traffic = _ncu_traffic(name)
+    passes = {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / v["launches"],
+                  "share": v["total_ms"] / sum(x["total_ms"] for x in prof.values()),
+                  "GBps": v["bytes_per_cell"] * v["fields_per_launch"] * v["cells"] / (v["total_ms"] / v["launches"] * 1e-3) / 1e9}
+              for k, v in prof.items()}
+    step_bytes = sum(v["bytes_per_cell"] * v["fields_per_launch"] * v["cells"] * v["launches"] for v in prof.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"3D Gaussian-random-field condensation {GRID_M}^3 x {STREAMS} streams (+ classical field), "
+                               f"FP32 KDK dt={w.phys.dt:.4e}, moments every {OUT_EVERY} steps",
+                   "grid": [GRID_M] * 3, "streams": STREAMS, "kdk_steps_per_step": OUT_EVERY,
+                   "batch_bytes": int(ens.psi.numel() * 8), "l2": "inputs larger than L2 (4.2 GB batch)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": name, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms},
+        "hbm_effective": {"algorithmic_GBps_whole_step": step_bytes / (ms * 1e-3) / 1e9 / world,
+                          "frac_of_peak": step_bytes / (ms * 1e-3) / 1e9 / world / peak,
+                          "compulsory_16B_frac": 16.0 * cell_updates / world / (ms * 1e-3) / 1e9 / peak},
+        "passes": passes,
+        "gpu_launches": int(launches),
+        "moments_last": {"Q": float(sc[-1, 0, 0]), "corr": float(sc[-1, 0, 1]), "mass": float(sc[-1, 0, 2])},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = _e2e(ens, w)
+        ens.close()
+        torch.cuda.empty_cache()
+        line["f64_plain"] = {"value": _f64_plain_rate(w), "unit": UNIT, "path": "TWA_F64_PLAIN, 1 stream + classical, 128^3"}
+        line["cufft_reference"] = {"value": _cufft_reference_rate(w), "unit": UNIT,
+                                   "path": "torch.fft (cuFFT) KDK step, 32 fields, reference only"}
+        cv, n, el = _oracle_rate(w)
+        line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                                "sample": f"2 streams of the 128^3 workload, {n} KDK steps in {el:.1f} s (FP64 scipy.fft)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _ncu_traffic(kernel_op: str):
+    """DRAM bytes per launch of the dominant pass from a committed ncu summary, if it matches this build."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        from paper_2310_07119_gb300.build import source_digest
+        if d.get("source_digest") != source_digest():
+            return None
+        return d.get("ops", {}).get(kernel_op, {}).get("dram_bytes_per_launch_full_size")
+    except Exception:
+        return None
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_twa(args)
+
+
+if __name__ == "__main__":
+    main()

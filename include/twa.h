@@ -1,0 +1,180 @@
+/*
+ * twa.h - C ABI of the GB300 truncated-Wigner (TWA) ensemble library (libtwa.so).
+ *
+ * Method (arXiv:2310.07119): a coherent state is represented by an ensemble of
+ * classical fields drawn from its Wigner function (Sec. III.A, Eq.
+ * eqn_stream_ensemble); every field evolves independently under the normalized
+ * Schroedinger-Poisson equations (Sec. III.C, Eq. mft_normed)
+ *     d psi/dt = -i ( -hbar/2 lap + V/hbar ) psi,    lap V = C |psi|^2,
+ * integrated by the pseudo-spectral kick-drift-kick split step of Sec. III.B.2;
+ * symmetric-operator expectation values are ensemble averages of Weyl symbols
+ * (Sec. III.B.3, Eq. E[op]) and the size of the quantum correction is Q(t)
+ * (Eq. Q).  "hbar" below always means hbar/m.
+ *
+ * Data layout (all device memory is owned by the caller unless stated):
+ *   field      : one realization on an nx*ny*nz grid, x fastest, interleaved
+ *                complex (float2 for TWA_F32, double2 for TWA_F64_PLAIN);
+ *   batch      : for each instance i (in order), (n_real[i] + 1) fields:
+ *                slot 0 is the classical field psi_cl (evolved without noise,
+ *                Sec. II.C), slots 1..n_real[i] the sampled streams.
+ *                Instance i starts at element offset sum_{j<i} (n_real[j]+1)*cells[j].
+ *   psi_cl     : for each instance, one complex128 field (FP64 input),
+ *                normalized to sum |psi|^2 dV = 1 (Sec. III.B.1).
+ *
+ * Every call returns 0 (TWA_OK) or a negative TWA_E* code; the message of the
+ * last failure is available from twa_last_error().  All calls that take a
+ * stream are asynchronous with respect to the host: they enqueue kernels on
+ * that stream and return.  Device-side failures (non-finite fields) are
+ * recorded in a device error word and reported by twa_sync_status().
+ * There is no CPU fallback: without a CUDA device every call fails with
+ * TWA_ECUDA.
+ */
+#ifndef TWA_H
+#define TWA_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TWA_OK           0
+#define TWA_EINVAL      -1   /* bad argument: null pointer, non-power-of-two or unsupported size */
+#define TWA_ENOMEM      -2   /* device allocation failed */
+#define TWA_ECUDA       -3   /* a CUDA runtime call failed (message has the CUDA error) */
+#define TWA_ETIMEOUT    -4   /* a device-side wait gave up (reported through twa_sync_status) */
+#define TWA_ENONFINITE  -5   /* a moments pass met a non-finite field value */
+
+#define TWA_F32          0   /* batched FP32 path: fused Stockham passes, realization pairs */
+#define TWA_F64_PLAIN    1   /* comparator: complex128, one realization per launch, no fusion */
+
+/* Number of FP64 scalars written per instance per output by twa_moments / twa_run. */
+#define TWA_NSCALARS     8
+#define TWA_S_Q          0   /* Q of Eq. Q: sum_g dV (mean|psi|^2 - |mean psi|^2) - M/(2 n) */
+#define TWA_S_CORR       1   /* ||<rho> - rho_cl||_2 / ||rho_cl||_2 */
+#define TWA_S_MASS       2   /* mean over streams of sum_g |psi|^2 dV (1 up to rounding) */
+#define TWA_S_MASS_CL    3   /* sum_g |psi_cl|^2 dV */
+#define TWA_S_NONFINITE  4   /* number of non-finite field values met (stored as double) */
+#define TWA_S_NK_SUM     5   /* sum_k <n_k> (total occupation, ~ n_tot); 0 if modes are off */
+#define TWA_S_DRHO_L2    6   /* ||<rho> - rho_cl||_2 */
+#define TWA_S_RHOCL_L2   7   /* ||rho_cl||_2 */
+
+/* Periodic box of Sec. III.B.1: dim axes of n[a] cells (powers of two, 8..2048;
+   unused axes = 1), side L on every axis, dx = L / n[a]. */
+typedef struct {
+    int dim;
+    int n[3];
+    double L;
+} twa_grid;
+
+/* Physical and numerical parameters shared by all instances of a handle.
+   hbar_m : hbar/m; C : coupling in lap V = C |psi|^2 (C = 4 pi G M_tot, Eq. mft_normed);
+   dt     : time step of the split step (Sec. III.B.2);
+   n_tot  : simulated particle number n^s_tot, used only by the sampling (Eq. sample);
+   noise_conv : 0 = complex variance 1/2 per mode (coherent-state Wigner function),
+                1 = variance 1/2 per real component (Eq. sample as printed);
+   precision  : TWA_F32 or TWA_F64_PLAIN;
+   want_modes : nonzero to allocate the spectral scratch used for per-mode moments. */
+typedef struct {
+    double hbar_m;
+    double C;
+    double dt;
+    double n_tot;
+    int noise_conv;
+    int precision;
+    int want_modes;
+} twa_params;
+
+/* Device FP64 outputs of one instance's moments (Eq. E[op]); any pointer may be NULL to skip it.
+   rho_mean[cells] = mean_s |psi_s|^2 - 1/(2 n dV)   (Weyl symbol of psi^dag psi)
+   psi_mean[2*cells] = mean_s psi_s                    (interleaved re, im)
+   rho_cl[cells]   = |psi_cl|^2
+   nk_mean[cells]  = mean_s |a_k|^2 - 1/2, a_k = sqrt(n dV / M) DFT(psi)_k (needs want_modes)
+   nk_var[cells]   = mean |a|^4 - mean |a|^2 - (mean |a|^2 - 1/2)^2  (Var of a^dag a)
+   scalars[TWA_NSCALARS] as defined above. Mode arrays are in FFT order (x fastest). */
+typedef struct {
+    double* rho_mean;
+    double* psi_mean;
+    double* rho_cl;
+    double* nk_mean;
+    double* nk_var;
+    double* scalars;
+} twa_moments_out;
+
+typedef struct twa_handle twa_handle;
+
+/* Create a handle for n_inst instances (grids[i], n_real[i] sampled streams each) sharing *p.
+   The handle owns its scratch: the Poisson buffer (8 bytes per cell per pair of slots in
+   FP32), the spectral scratch when want_modes is set, twiddle and phase tables, and the
+   graph and autotune state.  Must be called with the target device current.
+   Errors: TWA_EINVAL (sizes), TWA_ENOMEM, TWA_ECUDA. */
+int twa_create(twa_handle** out, const twa_grid* grids, const twa_params* p,
+               int n_inst, const int* n_real);
+
+/* Release everything the handle owns (never caller memory).  Accepts NULL. */
+int twa_destroy(twa_handle* h);
+
+/* Element count (complex elements) of the batch buffer for all instances. */
+size_t twa_batch_elems(const twa_handle* h);
+
+/* Sec. III.B.1, Eq. sample: slot 0 of every instance <- psi_cl (rounded to the path's
+   precision); slot s >= 1 <- psi_cl + sigma (zR + i zI), with zR, zI standard normals from
+   Philox4x32-10 (key = seed, counter = (cell, s, instance, 0)) through Box-Muller in FP64,
+   sigma^2 = v / (2 n_tot dV) per real component, v = 1/2 (noise_conv 0) or 1 (noise_conv 1).
+   psi_cl: device complex128, instances concatenated; psi: device batch buffer. */
+int twa_sample(twa_handle* h, const void* psi_cl, uint64_t seed, void* psi, void* stream);
+
+/* Advance every field of the batch by n_steps kick-drift-kick steps of Sec. III.B.2:
+   V(psi) -> exp(-i V dt / 2 hbar) -> FFT -> exp(-i hbar k^2 dt / 2) -> iFFT -> V(psi)
+   -> exp(-i V dt / 2 hbar), with V_k = -C rho_k / k^2, V_0 = 0.  Adjacent half kicks are
+   merged.  psi is read and written in place; asynchronous, no host synchronization. */
+int twa_step_batch(twa_handle* h, void* psi, int n_steps, void* stream);
+
+/* Ensemble moments of instance `inst` of the (synchronized) batch psi into *out
+   (Sec. III.B.3, Eq. Q).  Reductions accumulate in FP64 in a fixed order (bitwise
+   reproducible).  Per-mode outputs need want_modes. */
+int twa_moments(twa_handle* h, int inst, const void* psi, const twa_moments_out* out, void* stream);
+
+/* Continue a synchronized batch psi by n_steps KDK steps with moments at the start and every
+   out_every steps: scalars go to series[(o * n_inst + i) * TWA_NSCALARS + j] (device FP64) for
+   o = 0..n_steps/out_every.  Half kicks are merged across steps and the pending half kick is
+   applied on the fly by the moments; psi ends synchronized.  On the FP32 path every output
+   interval after the first is captured once as a CUDA graph and replayed (unless the pass
+   profiler is on).  n_steps must be a multiple of out_every. */
+int twa_advance(twa_handle* h, void* psi, int n_steps, int out_every, double* series, void* stream);
+
+/* Full run (Sec. III.B): twa_sample(psi_cl, seed) into psi_work, then twa_advance. */
+int twa_run(twa_handle* h, const void* psi_cl, uint64_t seed, int n_steps, int out_every,
+            void* psi_work, double* series, void* stream);
+
+/* Pass profiler.  While enabled, every FP32 line pass is bracketed by CUDA events on its own
+   stream and graph capture is skipped; twa_profile_read accumulates, per pass kind (op), the
+   number of launches and their total device time in ms since the last enable.  Ops are numbered
+   as in the library's pass table (TWA_PROF_NOPS kinds); bytes_per_cell receives the pass's
+   algorithmic DRAM traffic in bytes per cell of one launched field (pair or slot). */
+#define TWA_PROF_NOPS 12
+int twa_profile_enable(twa_handle* h, int on);
+int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_ms, double* bytes_per_cell,
+                     long long* fields_per_launch, long long* cells);
+
+/* Block on `stream` and report device-side failures recorded since the last call
+   (TWA_ENONFINITE) or TWA_OK.  Clears the device error word. */
+int twa_sync_status(twa_handle* h, void* stream);
+
+/* Message of the last failure on this handle (or of the last twa_create failure if h is NULL). */
+const char* twa_last_error(const twa_handle* h);
+
+/* Autotune the FP32 pass shapes (lines per CTA) for every instance by timing candidates on
+   `stream` with scratch fields; the choice is kept in the handle and, if cache_path is not
+   NULL, merged into that JSON file (read first if it exists).  psi: a batch buffer the tuner
+   may overwrite. */
+int twa_autotune(twa_handle* h, void* psi, const char* cache_path, void* stream);
+
+/* Number of kernel launches the last twa_step_batch / twa_run / twa_moments call enqueued. */
+long long twa_last_launch_count(const twa_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TWA_H */

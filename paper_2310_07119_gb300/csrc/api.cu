@@ -1,0 +1,1007 @@
+// api.cu - implementation of the C ABI in include/twa.h.
+//
+// Pipelines (per instance, FP32 path).  The state between steps is "drifted, kick pending": the
+// kick of step s+1 is merged with the closing half kick of step s (Sec. III.B.2), and the pending
+// half kick is applied on the fly by the moment kernels.
+//   1D : one on-chip pass per launch runs many steps (whole field in registers).
+//   2D : x rows  [kick + drift_x]  -> y cols [drift_y + packed density + FFT_y]
+//        -> x rows [FFT_x, Poisson, iFFT_x] -> y cols [iFFT_y]                      (4 passes/step)
+//   3D : x [iFFT_x of V + kick + drift_x] -> y [drift_y] -> z [drift_z + density + FFT_z]
+//        -> x [FFT_x] -> y [FFT_y, Poisson, iFFT_y] -> z [iFFT_z]                   (6 passes/step)
+//        V stays spectral along x between steps; its inverse is fused into the next kick.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <iterator>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <set>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "passes.cuh"
+#include "twa.h"
+
+using namespace twa;
+
+static_assert(OP_COUNT == TWA_PROF_NOPS, "profiler op table out of sync with the pass kinds");
+
+namespace {
+
+constexpr int MODE_1D = 0, MODE_2D = 1, MODE_3D = 2;
+
+struct Inst {
+    int dim = 1;
+    int n[3] = {1, 1, 1};
+    int lg[3] = {0, 0, 0};
+    long long cells = 0;
+    double L = 1.0, dV = 1.0;
+    int n_real = 0, n_slots = 0, n_pairs = 0;
+    size_t off = 0;
+    int mode = MODE_1D;
+    // FP32 path
+    float2* vc = nullptr;
+    float2* spec = nullptr;
+    float2* ph[3] = {nullptr, nullptr, nullptr};
+    float2* ph_lo[3] = {nullptr, nullptr, nullptr};
+    float* k2[3] = {nullptr, nullptr, nullptr};
+    double* part_r = nullptr;
+    double* part_m = nullptr;
+    std::map<int, int> lines;  // (axis * 64 + op) -> lines per CTA
+    // FP64 path
+    double2* work64 = nullptr;
+    double2* spec64 = nullptr;
+    double* acc64 = nullptr;
+    double* acc64m = nullptr;
+    double* bad64 = nullptr;
+    double2* tw64[3] = {nullptr, nullptr, nullptr};
+    double2* ph64[3] = {nullptr, nullptr, nullptr};
+    double* k264[3] = {nullptr, nullptr, nullptr};
+};
+
+std::string g_create_error;
+
+}  // namespace
+
+struct twa_handle {
+    twa_params p{};
+    std::vector<Inst> in;
+    std::string err;
+    int* d_err = nullptr;
+    int* d_counter = nullptr;
+    double* d_cur = nullptr;  // [n_inst][TWA_NSCALARS] scalars of the current output
+    std::map<int, float4*> tw32;
+    std::set<long long> prepared;
+    std::vector<void*> allocs;
+    long long launches = 0;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_launches = 0;
+    const void* g_psi = nullptr;
+    const void* g_series = nullptr;
+    int g_out_every = -1;
+    // pass profiler
+    bool prof_on = false;
+    struct ProfRec {
+        int op;
+        cudaEvent_t a, b;
+        long long fields, cells;
+    };
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    long long prof_launches[OP_COUNT] = {};
+    double prof_ms[OP_COUNT] = {};
+    long long prof_fields[OP_COUNT] = {};
+    long long prof_cells[OP_COUNT] = {};
+};
+
+namespace {
+
+// kick = -frac dt C / (hbar cells) in FP64, carried as float hi + lo (the stored Poisson field is
+// W = iFFT(FFT(rho) / k^2), so V = -C W / cells and theta = kick W).
+void split_kick(const twa_handle* h, const Inst& I, double frac, float& hi, float& lo) {
+    const double k = -frac * h->p.dt * h->p.C / (h->p.hbar_m * (double)I.cells);
+    hi = (float)k;
+    lo = (float)(k - (double)hi);
+}
+
+int fail(twa_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(h, TWA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+int dalloc(twa_handle* h, T** ptr, size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, TWA_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    h->allocs.push_back(p);
+    *ptr = static_cast<T*>(p);
+    return 0;
+}
+
+template <class T>
+int upload(twa_handle* h, T** dst, const std::vector<T>& v) {
+    int rc = dalloc(h, dst, v.size());
+    if (rc) return rc;
+    CU(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return 0;
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+// Wavenumber of FFT index j on an axis of n cells and side L: 2 pi m / L, m in {0..n/2-1, -n/2..-1}.
+double wavenumber(int j, int n, double L) {
+    const int m = (j < n / 2) ? j : j - n;
+    return 2.0 * M_PI * (double)m / L;
+}
+
+// exp(-i theta) with theta reduced mod 2 pi in FP64 first.
+void phase_of(double theta, double& c, double& s) {
+    const double r = std::fmod(theta, 2.0 * M_PI);
+    c = std::cos(r);
+    s = -std::sin(r);
+}
+
+int key_of(int axis, int op) { return axis * 64 + op; }
+
+}  // namespace
+struct twa_handle;
+namespace {
+void split_kick(const twa_handle* h, const Inst& I, double frac, float& hi, float& lo);
+
+int default_lines(int N, bool strided, int op) {
+    const int T = plan_threads_per_line(N);
+    if (op == OP_STEPS_1D) return std::max(1, 128 / T);
+    if (strided) return std::max(4, 256 / T);
+    return std::max(1, 256 / T);
+}
+
+int dispatch(int N, const LaunchCfg& c, const PassArgs& a, cudaStream_t st, bool prep) {
+    switch (N) {
+        case 8: return launch_line<8>(c, a, st, prep);
+        case 16: return launch_line<16>(c, a, st, prep);
+        case 32: return launch_line<32>(c, a, st, prep);
+        case 64: return launch_line<64>(c, a, st, prep);
+        case 128: return launch_line<128>(c, a, st, prep);
+        case 256: return launch_line<256>(c, a, st, prep);
+        case 512: return launch_line<512>(c, a, st, prep);
+        case 1024: return launch_line<1024>(c, a, st, prep);
+        case 2048: return launch_line<2048>(c, a, st, prep);
+        default: return -1;
+    }
+}
+
+bool variant_ok(int N, int op, bool strided, int lines) {
+    switch (N) {
+        case 8: return has_variant<8>(op, strided, lines);
+        case 16: return has_variant<16>(op, strided, lines);
+        case 32: return has_variant<32>(op, strided, lines);
+        case 64: return has_variant<64>(op, strided, lines);
+        case 128: return has_variant<128>(op, strided, lines);
+        case 256: return has_variant<256>(op, strided, lines);
+        case 512: return has_variant<512>(op, strided, lines);
+        case 1024: return has_variant<1024>(op, strided, lines);
+        case 2048: return has_variant<2048>(op, strided, lines);
+        default: return false;
+    }
+}
+
+#define RC(x)                \
+    do {                     \
+        int rc_ = (x);       \
+        if (rc_) return rc_; \
+    } while (0)
+
+int prof_events(twa_handle* h, cudaEvent_t* a, cudaEvent_t* b) {
+    for (cudaEvent_t* e : {a, b}) {
+        if (h->prof_pool.empty()) {
+            cudaEvent_t n;
+            CU(cudaEventCreate(&n));
+            h->prof_pool.push_back(n);
+        }
+        *e = h->prof_pool.back();
+        h->prof_pool.pop_back();
+    }
+    return 0;
+}
+
+// One line pass over `fields` fields (pairs or slots) of instance I.
+int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_frac, float2* buf, float2* out, int fields,
+             cudaStream_t st, int nsteps = 0, int force_lines = 0, float post = 1.0f) {
+    const int N = I.n[axis];
+    const bool strided = axis > 0;
+    int lines = force_lines;
+    if (!lines) {
+        auto it = I.lines.find(key_of(axis, op));
+        lines = (it != I.lines.end()) ? it->second : default_lines(N, strided, op);
+    }
+    if (!variant_ok(N, op, strided, lines))
+        return fail(h, TWA_EINVAL, "no pass variant for N=" + std::to_string(N) + " op=" + std::to_string(op) +
+                                       " lines=" + std::to_string(lines));
+    PassArgs a{};
+    a.psi = psi;
+    a.buf = buf;
+    a.out = out;
+    a.tw = h->tw32[N];
+    a.ph = I.ph[axis];
+    a.ph_lo = I.ph_lo[axis];
+    a.post = post;
+    a.k2x = I.k2[0];
+    a.k2y = I.k2[1];
+    a.k2z = I.k2[2];
+    split_kick(h, I, kick_frac, a.kick, a.kick_lo);
+    split_kick(h, I, 1.0, a.kick2, a.kick2_lo);
+    a.cells = I.cells;
+    a.n_slots = I.n_slots;
+    a.n_pairs = I.n_pairs;
+    a.lx = I.lg[0];
+    a.lxy = I.lg[0] + I.lg[1];
+    a.nsteps = nsteps;
+    long long stride = 1;
+    for (int b = 0; b < axis; ++b) stride *= I.n[b];
+    a.S = (int)stride;
+    a.Qn = (int)stride;
+    a.OS = stride * N;
+    LaunchCfg c{};
+    c.op = op;
+    c.strided = strided;
+    c.lines = lines;
+    if (op == OP_STEPS_1D) {
+        c.grid = dim3((unsigned)((I.n_pairs + lines - 1) / lines), 1, 1);
+    } else if (strided) {
+        const long long tq = (stride + lines - 1) / lines;
+        const long long outer = I.cells / (stride * N);
+        c.grid = dim3((unsigned)(tq * outer), (unsigned)fields, 1);
+    } else {
+        const long long rows = I.cells / N;
+        c.grid = dim3((unsigned)((rows + lines - 1) / lines), (unsigned)fields, 1);
+    }
+    const long long pk = ((long long)N << 24) | ((long long)op << 16) | ((long long)strided << 12) | lines;
+    if (!h->prepared.count(pk)) {
+        if (dispatch(N, c, a, st, true) != 0) return fail(h, TWA_ECUDA, "cudaFuncSetAttribute failed");
+        h->prepared.insert(pk);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->prof_on) {
+        RC(prof_events(h, &e0, &e1));
+        CU(cudaEventRecord(e0, st));
+    }
+    if (dispatch(N, c, a, st, false) != 0) return fail(h, TWA_EINVAL, "pass dispatch failed");
+    if (h->prof_on) {
+        CU(cudaEventRecord(e1, st));
+        const long long nf = (op == OP_STEPS_1D) ? (long long)I.n_pairs * nsteps : (long long)fields;
+        h->prof_pending.push_back({op, e0, e1, nf, I.cells});
+    }
+    ++h->launches;
+    return 0;
+}
+
+
+float2* inst_psi(Inst& I, void* psi) { return static_cast<float2*>(psi) + I.off; }
+
+// V of every field from its density (a synchronized batch, nothing pending).
+int poisson_init(twa_handle* h, Inst& I, float2* psi, cudaStream_t st) {
+    const int P = I.n_pairs;
+    switch (I.mode) {
+        case MODE_1D:
+            RC(run_pass(h, I, psi, 0, OP_RHO_FWD, 0.0, I.vc, nullptr, P, st, 0, 1));
+            RC(run_pass(h, I, psi, 0, OP_MUL_INV, 0.0, I.vc, nullptr, P, st, 0, 1));
+            break;
+        case MODE_2D:
+            RC(run_pass(h, I, psi, 1, OP_RHO_FWD, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 0, OP_FWD_MUL_INV, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 1, OP_INV, 0.0, I.vc, nullptr, P, st));
+            break;
+        default:
+            RC(run_pass(h, I, psi, 2, OP_RHO_FWD, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 0, OP_FWD, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 1, OP_FWD_MUL_INV, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 2, OP_INV, 0.0, I.vc, nullptr, P, st));
+    }
+    return 0;
+}
+
+// n steps; the first kick is the fraction a_first of a full kick (1/2 after a synchronized state).
+int steps_f32(twa_handle* h, Inst& I, float2* psi, int n, double a_first, cudaStream_t st) {
+    const int P = I.n_pairs;
+    if (n <= 0) return 0;
+    if (I.mode == MODE_1D) return run_pass(h, I, psi, 0, OP_STEPS_1D, a_first, I.vc, nullptr, P, st, n);
+    for (int s = 0; s < n; ++s) {
+        const double k = (s == 0) ? a_first : 1.0;
+        if (I.mode == MODE_2D) {
+            RC(run_pass(h, I, psi, 0, OP_KICK_DRIFT, k, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 1, OP_DRIFT_RHO, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 0, OP_FWD_MUL_INV, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 1, OP_INV, 0.0, I.vc, nullptr, P, st));
+        } else {
+            RC(run_pass(h, I, psi, 0, OP_KICK_DRIFT_VINV, k, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 1, OP_DRIFT, 0.0, I.vc, nullptr, I.n_slots, st));
+            RC(run_pass(h, I, psi, 2, OP_DRIFT_RHO, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 0, OP_FWD, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 1, OP_FWD_MUL_INV, 0.0, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 2, OP_INV, 0.0, I.vc, nullptr, P, st));
+        }
+    }
+    return 0;
+}
+
+int closing_kick(twa_handle* h, Inst& I, float2* psi, double frac, cudaStream_t st) {
+    if (I.mode == MODE_3D) return run_pass(h, I, psi, 0, OP_KICK_VINV, frac, I.vc, nullptr, I.n_pairs, st);
+    float k, kl;
+    split_kick(h, I, frac, k, kl);
+    launch_kick_pairs(psi, I.vc, I.cells, I.n_slots, k, kl, st);
+    ++h->launches;
+    return 0;
+}
+
+// Moments with a pending kick (0 for a synchronized batch); scalars into `scalars` (device).
+int moments_f32(twa_handle* h, Inst& I, float2* psi, double pend, const twa_moments_out* o, double* scalars,
+                cudaStream_t st) {
+    const bool v_spec = (I.mode == MODE_3D) && pend != 0.0;
+    float pk, pkl;
+    split_kick(h, I, pend, pk, pkl);
+    if (v_spec) RC(run_pass(h, I, psi, 0, OP_INV, 0.0, I.vc, nullptr, I.n_pairs, st));
+    const int nb = moments_blocks(I.cells);
+    const double ns = (double)I.n_real;
+    const double weyl = 1.0 / (2.0 * h->p.n_tot * I.dV);
+    launch_moments_real(psi, I.vc, I.cells, I.n_slots, pk, pkl, 1.0 / ns, weyl, o ? o->rho_mean : nullptr,
+                        o ? o->psi_mean : nullptr, o ? o->rho_cl : nullptr, I.part_r, st);
+    ++h->launches;
+    int nbm = 0;
+    if (h->p.want_modes && I.spec) {
+        RC(run_pass(h, I, psi, 0, OP_KICK_FWD_OUT, pend, I.vc, I.spec, I.n_pairs, st, 0, I.mode == MODE_1D ? 1 : 0));
+        for (int ax = 1; ax < I.dim; ++ax) RC(run_pass(h, I, psi, ax, OP_FWD, 0.0, I.spec, nullptr, I.n_slots, st));
+        launch_moments_modes(I.spec, I.cells, I.n_slots, h->p.n_tot * I.dV / (double)I.cells, 1.0 / ns,
+                             o ? o->nk_mean : nullptr, o ? o->nk_var : nullptr, I.part_m, st);
+        ++h->launches;
+        nbm = nb;
+    }
+    launch_finish_scalars(I.part_r, nb, I.part_m, nbm, I.dV, (double)I.cells / (2.0 * h->p.n_tot), scalars, h->d_err, st);
+    ++h->launches;
+    // restore the x-spectral Poisson field: the unnormalized forward transform of the inverse
+    // multiplies by N_x, which the post factor removes
+    if (v_spec) RC(run_pass(h, I, psi, 0, OP_FWD, 0.0, I.vc, nullptr, I.n_pairs, st, 0, 0, 1.0f / (float)I.n[0]));
+    return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 plain path.
+Geom64 geom64(const Inst& I) {
+    Geom64 g{};
+    g.dim = I.dim;
+    for (int a = 0; a < 3; ++a) g.n[a] = I.n[a];
+    g.cells = I.cells;
+    return g;
+}
+Tables64 tables64(const Inst& I) {
+    Tables64 t{};
+    for (int a = 0; a < 3; ++a) {
+        t.tw[a] = I.tw64[a];
+        t.ph[a] = I.ph64[a];
+        t.k2[a] = I.k264[a];
+    }
+    return t;
+}
+
+int poisson_f64(twa_handle* h, Inst& I, double2* f, cudaStream_t st) {
+    const Geom64 g = geom64(I);
+    const Tables64 t = tables64(I);
+    launch_f64_rho(f, I.work64, I.cells, st, &h->launches);
+    launch_f64_fft3(I.work64, g, t, false, st, &h->launches);
+    launch_f64_poisson_mul(I.work64, g, t, -h->p.C / (double)I.cells, st, &h->launches);
+    launch_f64_fft3(I.work64, g, t, true, st, &h->launches);
+    return 0;
+}
+
+int step_batch_f64(twa_handle* h, Inst& I, double2* psi, int n, cudaStream_t st) {
+    const Geom64 g = geom64(I);
+    const Tables64 t = tables64(I);
+    const double kh = h->p.dt / (2.0 * h->p.hbar_m), kf = h->p.dt / h->p.hbar_m;
+    for (int s = 0; s < I.n_slots; ++s) {
+        double2* f = psi + (size_t)s * I.cells;
+        RC(poisson_f64(h, I, f, st));
+        launch_f64_kick(f, I.work64, I.cells, kh, st, &h->launches);
+        for (int k = 0; k < n; ++k) {
+            launch_f64_fft3(f, g, t, false, st, &h->launches);
+            launch_f64_kinetic(f, g, t, st, &h->launches);
+            launch_f64_fft3(f, g, t, true, st, &h->launches);
+            RC(poisson_f64(h, I, f, st));
+            launch_f64_kick(f, I.work64, I.cells, (k == n - 1) ? kh : kf, st, &h->launches);
+        }
+    }
+    return 0;
+}
+
+int moments_f64(twa_handle* h, Inst& I, double2* psi, const twa_moments_out* o, double* scalars, cudaStream_t st) {
+    const Geom64 g = geom64(I);
+    const Tables64 t = tables64(I);
+    CU(cudaMemsetAsync(I.bad64, 0, sizeof(double), st));
+    const bool modes = h->p.want_modes && I.spec64;
+    for (int s = 1; s < I.n_slots; ++s) {
+        double2* f = psi + (size_t)s * I.cells;
+        launch_f64_moments_accum(f, nullptr, I.cells, 0.0, s == 1, I.acc64, I.bad64, st, &h->launches);
+        if (modes) {
+            CU(cudaMemcpyAsync(I.spec64, f, I.cells * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+            launch_f64_fft3(I.spec64, g, t, false, st, &h->launches);
+            launch_f64_modes_accum(I.spec64, I.cells, h->p.n_tot * I.dV / (double)I.cells, s == 1, I.acc64m, st,
+                                   &h->launches);
+        }
+    }
+    launch_f64_moments_finish(I.acc64, modes ? I.acc64m : nullptr, psi, I.cells, I.n_real,
+                              1.0 / (2.0 * h->p.n_tot * I.dV), I.dV, (double)I.cells / (2.0 * h->p.n_tot),
+                              o ? o->rho_mean : nullptr, o ? o->psi_mean : nullptr, o ? o->rho_cl : nullptr,
+                              o ? o->nk_mean : nullptr, o ? o->nk_var : nullptr, I.part_r, I.part_m, I.bad64, scalars,
+                              h->d_err, st, &h->launches);
+    return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+int build_tables(twa_handle* h, Inst& I) {
+    const double hb = h->p.hbar_m, dt = h->p.dt;
+    for (int a = 0; a < 3; ++a) {
+        const int n = I.n[a];
+        std::vector<float> k2f(n);
+        std::vector<double> k2d(n);
+        std::vector<float2> phf(n), phl(n);
+        std::vector<double2> phd(n), twd(n);
+        for (int j = 0; j < n; ++j) {
+            const double k = (a < I.dim) ? wavenumber(j, n, I.L) : 0.0;
+            k2d[j] = k * k;
+            k2f[j] = (float)(k * k);
+            double c, s;
+            phase_of(hb * k * k * dt / 2.0, c, s);
+            phd[j] = make_double2(c, s);
+            phf[j] = make_float2((float)(c / n), (float)(s / n));
+            phl[j] = make_float2((float)(c / n - (double)phf[j].x), (float)(s / n - (double)phf[j].y));
+            const double ang = -2.0 * M_PI * (double)j / (double)n;
+            twd[j] = make_double2(std::cos(ang), std::sin(ang));
+        }
+        if (h->p.precision == TWA_F32) {
+            RC(upload(h, &I.k2[a], k2f));
+            RC(upload(h, &I.ph[a], phf));
+            RC(upload(h, &I.ph_lo[a], phl));
+            if (a < I.dim && !h->tw32.count(n)) {
+                std::vector<float4> tw(n);
+                for (int j = 0; j < n; ++j) {
+                    const float hx = (float)twd[j].x, hy = (float)twd[j].y;
+                    tw[j] = make_float4(hx, hy, (float)(twd[j].x - (double)hx), (float)(twd[j].y - (double)hy));
+                }
+                float4* d = nullptr;
+                RC(upload(h, &d, tw));
+                h->tw32[n] = d;
+            }
+        } else {
+            RC(upload(h, &I.k264[a], k2d));
+            RC(upload(h, &I.ph64[a], phd));
+            RC(upload(h, &I.tw64[a], twd));
+        }
+    }
+    return 0;
+}
+
+}  // namespace
+
+namespace twa {
+int plan_threads_per_line(int n) {
+    switch (n) {
+        case 8: return Plan<8>::T;
+        case 16: return Plan<16>::T;
+        case 32: return Plan<32>::T;
+        case 64: return Plan<64>::T;
+        case 128: return Plan<128>::T;
+        case 256: return Plan<256>::T;
+        case 512: return Plan<512>::T;
+        case 1024: return Plan<1024>::T;
+        case 2048: return Plan<2048>::T;
+        default: return 1;
+    }
+}
+}  // namespace twa
+
+// =============================================================================================
+extern "C" {
+
+int twa_create(twa_handle** out, const twa_grid* grids, const twa_params* p, int n_inst, const int* n_real) {
+    twa_handle* h = nullptr;
+    if (!out || !grids || !p || !n_real || n_inst <= 0) return fail(nullptr, TWA_EINVAL, "twa_create: null argument");
+    *out = nullptr;
+    if (p->precision != TWA_F32 && p->precision != TWA_F64_PLAIN)
+        return fail(nullptr, TWA_EINVAL, "twa_create: unknown precision");
+    if (!(p->hbar_m > 0) || !(p->dt > 0) || !(p->n_tot > 0))
+        return fail(nullptr, TWA_EINVAL, "twa_create: hbar_m, dt and n_tot must be positive");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, TWA_ECUDA, "twa_create: no CUDA device");
+    }
+    h = new twa_handle();
+    h->p = *p;
+    size_t off = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        Inst I;
+        const twa_grid& g = grids[i];
+        if (g.dim < 1 || g.dim > 3 || n_real[i] < 1 || !(g.L > 0)) {
+            twa_destroy(h);
+            return fail(nullptr, TWA_EINVAL, "twa_create: bad grid or realization count");
+        }
+        I.dim = g.dim;
+        I.L = g.L;
+        I.cells = 1;
+        for (int a = 0; a < 3; ++a) {
+            I.n[a] = (a < g.dim) ? g.n[a] : 1;
+            if (a < g.dim && (!pow2(I.n[a]) || I.n[a] < 8 || I.n[a] > 2048)) {
+                twa_destroy(h);
+                return fail(nullptr, TWA_EINVAL, "twa_create: axis lengths must be powers of two in [8, 2048]");
+            }
+            I.lg[a] = ilog2(I.n[a]);
+            I.cells *= I.n[a];
+        }
+        I.dV = 1.0;
+        for (int a = 0; a < g.dim; ++a) I.dV *= g.L / I.n[a];
+        I.n_real = n_real[i];
+        I.n_slots = n_real[i] + 1;
+        I.n_pairs = (I.n_slots + 1) / 2;
+        I.off = off;
+        off += (size_t)I.n_slots * I.cells;
+        I.mode = (g.dim == 1) ? MODE_1D : (g.dim == 2 ? MODE_2D : MODE_3D);
+        h->in.push_back(I);
+    }
+    int rc = 0;
+    auto bail = [&](int code) {
+        g_create_error = h->err;
+        twa_destroy(h);
+        return code;
+    };
+    if ((rc = dalloc(h, &h->d_err, 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_counter, 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_cur, (size_t)n_inst * TWA_NSCALARS))) return bail(rc);
+    cudaMemset(h->d_err, 0, sizeof(int));
+    cudaMemset(h->d_counter, 0, sizeof(int));
+    for (auto& I : h->in) {
+        if ((rc = build_tables(h, I))) return bail(rc);
+        const int nb = moments_blocks(I.cells);
+        if ((rc = dalloc(h, &I.part_r, (size_t)nb * NP_REAL))) return bail(rc);
+        if ((rc = dalloc(h, &I.part_m, (size_t)nb * NP_MODES))) return bail(rc);
+        if (p->precision == TWA_F32) {
+            if ((rc = dalloc(h, &I.vc, (size_t)I.n_pairs * I.cells))) return bail(rc);
+            cudaMemset(I.vc, 0, (size_t)I.n_pairs * I.cells * sizeof(float2));
+            if (p->want_modes && (rc = dalloc(h, &I.spec, (size_t)I.n_slots * I.cells))) return bail(rc);
+        } else {
+            if ((rc = dalloc(h, &I.work64, (size_t)I.cells))) return bail(rc);
+            if ((rc = dalloc(h, &I.acc64, (size_t)3 * I.cells))) return bail(rc);
+            if ((rc = dalloc(h, &I.bad64, 1))) return bail(rc);
+            if (p->want_modes) {
+                if ((rc = dalloc(h, &I.spec64, (size_t)I.cells))) return bail(rc);
+                if ((rc = dalloc(h, &I.acc64m, (size_t)2 * I.cells))) return bail(rc);
+            }
+        }
+    }
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_b, cudaEventDisableTiming) != cudaSuccess) {
+        h->err = "stream/event creation failed";
+        return bail(TWA_ECUDA);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        h->err = "device synchronize after setup failed";
+        return bail(TWA_ECUDA);
+    }
+    *out = h;
+    return TWA_OK;
+}
+
+int twa_destroy(twa_handle* h) {
+    if (!h) return TWA_OK;
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (auto& r : h->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->ev_a) cudaEventDestroy(h->ev_a);
+    if (h->ev_b) cudaEventDestroy(h->ev_b);
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+    return TWA_OK;
+}
+
+size_t twa_batch_elems(const twa_handle* h) {
+    if (!h) return 0;
+    size_t n = 0;
+    for (const auto& I : h->in) n += (size_t)I.n_slots * I.cells;
+    return n;
+}
+
+int twa_sample(twa_handle* h, const void* psi_cl, uint64_t seed, void* psi, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!psi_cl || !psi) return fail(h, TWA_EINVAL, "twa_sample: null buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    h->launches = 0;
+    size_t cl_off = 0;
+    for (size_t i = 0; i < h->in.size(); ++i) {
+        Inst& I = h->in[i];
+        const double var_mode = h->p.noise_conv == 0 ? 0.5 : 1.0;
+        const double sigma = std::sqrt(var_mode / (2.0 * h->p.n_tot * I.dV));
+        const double2* cl = static_cast<const double2*>(psi_cl) + cl_off;
+        if (h->p.precision == TWA_F32)
+            launch_sample_f32(cl, static_cast<float2*>(psi) + I.off, I.cells, I.n_slots, seed, (int)i, sigma, st);
+        else
+            launch_sample_f64(cl, static_cast<double2*>(psi) + I.off, I.cells, I.n_slots, seed, (int)i, sigma, st);
+        ++h->launches;
+        cl_off += (size_t)I.cells;
+    }
+    CU(cudaGetLastError());
+    return TWA_OK;
+}
+
+int twa_step_batch(twa_handle* h, void* psi, int n_steps, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!psi || n_steps < 0) return fail(h, TWA_EINVAL, "twa_step_batch: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    h->launches = 0;
+    if (n_steps == 0) return TWA_OK;
+    for (auto& I : h->in) {
+        if (h->p.precision == TWA_F32) {
+            float2* f = inst_psi(I, psi);
+            RC(poisson_init(h, I, f, st));
+            RC(steps_f32(h, I, f, n_steps, 0.5, st));
+            RC(closing_kick(h, I, f, 0.5, st));
+        } else {
+            RC(step_batch_f64(h, I, static_cast<double2*>(psi) + I.off, n_steps, st));
+        }
+    }
+    CU(cudaGetLastError());
+    return TWA_OK;
+}
+
+int twa_moments(twa_handle* h, int inst, const void* psi, const twa_moments_out* out, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!psi || !out || inst < 0 || inst >= (int)h->in.size()) return fail(h, TWA_EINVAL, "twa_moments: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    h->launches = 0;
+    Inst& I = h->in[inst];
+    double* sc = out->scalars ? out->scalars : h->d_cur + (size_t)inst * TWA_NSCALARS;
+    if (h->p.precision == TWA_F32)
+        RC(moments_f32(h, I, inst_psi(I, const_cast<void*>(psi)), 0.0, out, sc, st));
+    else
+        RC(moments_f64(h, I, static_cast<double2*>(const_cast<void*>(psi)) + I.off, out, sc, st));
+    CU(cudaGetLastError());
+    return TWA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One output interval of the FP32 run for all instances: steps, moments (pending half kick), store.
+int run_interval_f32(twa_handle* h, void* psi, int out_every, double a_first, double* series, cudaStream_t st) {
+    for (size_t i = 0; i < h->in.size(); ++i) {
+        Inst& I = h->in[i];
+        float2* f = inst_psi(I, psi);
+        RC(steps_f32(h, I, f, out_every, a_first, st));
+        RC(moments_f32(h, I, f, 0.5, nullptr, h->d_cur + i * TWA_NSCALARS, st));
+    }
+    launch_store_series(h->d_cur, series, h->d_counter, (int)h->in.size() * TWA_NSCALARS, st);
+    ++h->launches;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int twa_advance(twa_handle* h, void* psi_work, int n_steps, int out_every, double* series, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!psi_work || !series || out_every <= 0 || n_steps < 0 || n_steps % out_every)
+        return fail(h, TWA_EINVAL, "twa_advance: bad argument (n_steps must be a multiple of out_every)");
+    cudaStream_t user = (cudaStream_t)stream;
+    long long total = 0;
+    h->launches = 0;
+    const int n_out = n_steps / out_every;
+    CU(cudaMemsetAsync(h->d_counter, 0, sizeof(int), user));
+    if (h->p.precision == TWA_F64_PLAIN) {
+        for (int o = 0; o <= n_out; ++o) {
+            if (o > 0) {
+                RC(twa_step_batch(h, psi_work, out_every, stream));
+                total += h->launches;
+            }
+            h->launches = 0;
+            for (size_t i = 0; i < h->in.size(); ++i) {
+                Inst& I = h->in[i];
+                RC(moments_f64(h, I, static_cast<double2*>(psi_work) + I.off, nullptr, h->d_cur + i * TWA_NSCALARS, user));
+            }
+            launch_store_series(h->d_cur, series, h->d_counter, (int)h->in.size() * TWA_NSCALARS, user);
+            total += h->launches + 1;
+        }
+        h->launches = total;
+        CU(cudaGetLastError());
+        return TWA_OK;
+    }
+    // FP32: eager prologue and first interval, then one captured graph per later interval.
+    const double kh = 0.5, kf = 1.0;
+    for (size_t i = 0; i < h->in.size(); ++i) {
+        Inst& I = h->in[i];
+        float2* f = inst_psi(I, psi_work);
+        RC(poisson_init(h, I, f, user));
+        RC(moments_f32(h, I, f, 0.0, nullptr, h->d_cur + i * TWA_NSCALARS, user));
+    }
+    launch_store_series(h->d_cur, series, h->d_counter, (int)h->in.size() * TWA_NSCALARS, user);
+    ++h->launches;
+    if (n_out >= 1) RC(run_interval_f32(h, psi_work, out_every, kh, series, user));
+    total += h->launches;
+    if (n_out >= 2 && h->prof_on) {
+        for (int o = 2; o <= n_out; ++o) RC(run_interval_f32(h, psi_work, out_every, kf, series, user));
+        total += h->launches;
+    } else if (n_out >= 2) {
+        const bool reuse = h->gexec && h->g_psi == psi_work && h->g_series == series && h->g_out_every == out_every;
+        if (!reuse) {
+            if (h->gexec) {
+                cudaGraphExecDestroy(h->gexec);
+                h->gexec = nullptr;
+            }
+            CU(cudaEventRecord(h->ev_a, user));
+            CU(cudaStreamWaitEvent(h->cap, h->ev_a, 0));
+            h->launches = 0;
+            CU(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+            int rc = run_interval_f32(h, psi_work, out_every, kf, series, h->cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(h->cap, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ce != cudaSuccess) return fail(h, TWA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&h->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return fail(h, TWA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+            h->graph_launches = h->launches;
+            h->g_psi = psi_work;
+            h->g_series = series;
+            h->g_out_every = out_every;
+        } else {
+            CU(cudaEventRecord(h->ev_a, user));
+            CU(cudaStreamWaitEvent(h->cap, h->ev_a, 0));
+        }
+        for (int o = 2; o <= n_out; ++o) CU(cudaGraphLaunch(h->gexec, h->cap));
+        total += h->graph_launches * (n_out - 1);
+        CU(cudaEventRecord(h->ev_b, h->cap));
+        CU(cudaStreamWaitEvent(user, h->ev_b, 0));
+    }
+    h->launches = 0;
+    for (auto& I : h->in) RC(closing_kick(h, I, inst_psi(I, psi_work), kh, user));
+    total += h->launches;
+    h->launches = total;
+    CU(cudaGetLastError());
+    return TWA_OK;
+}
+
+int twa_run(twa_handle* h, const void* psi_cl, uint64_t seed, int n_steps, int out_every, void* psi_work,
+            double* series, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!psi_cl || !psi_work || !series || out_every <= 0 || n_steps < 0 || n_steps % out_every)
+        return fail(h, TWA_EINVAL, "twa_run: bad argument (n_steps must be a multiple of out_every)");
+    RC(twa_sample(h, psi_cl, seed, psi_work, stream));
+    const long long ns = h->launches;
+    RC(twa_advance(h, psi_work, n_steps, out_every, series, stream));
+    h->launches += ns;
+    return TWA_OK;
+}
+
+int twa_sync_status(twa_handle* h, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    int w = 0;
+    CU(cudaMemcpy(&w, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (w & 1) return fail(h, TWA_ENONFINITE, "a moments pass met a non-finite field value");
+    return TWA_OK;
+}
+
+const char* twa_last_error(const twa_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int twa_profile_enable(twa_handle* h, int on) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    CU(cudaDeviceSynchronize());
+    for (auto& r : h->prof_pending) {
+        h->prof_pool.push_back(r.a);
+        h->prof_pool.push_back(r.b);
+    }
+    h->prof_pending.clear();
+    for (int i = 0; i < OP_COUNT; ++i) {
+        h->prof_launches[i] = 0;
+        h->prof_ms[i] = 0.0;
+    }
+    h->prof_on = on != 0;
+    return TWA_OK;
+}
+
+int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_ms, double* bytes_per_cell,
+                     long long* fields_per_launch, long long* cells) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (op < 0 || op >= OP_COUNT) return fail(h, TWA_EINVAL, "twa_profile_read: bad op");
+    for (auto& r : h->prof_pending) {
+        CU(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, r.a, r.b));
+        h->prof_launches[r.op] += 1;
+        h->prof_ms[r.op] += ms;
+        h->prof_fields[r.op] = r.fields;
+        h->prof_cells[r.op] = r.cells;
+        h->prof_pool.push_back(r.a);
+        h->prof_pool.push_back(r.b);
+    }
+    h->prof_pending.clear();
+    // Algorithmic DRAM bytes per cell of one launched field (a pair of slots or one slot):
+    // every complex value read or written once (8 bytes), the Poisson field once per pair.
+    static const double bpc[OP_COUNT] = {
+        16.0,  // OP_DRIFT: psi read + write
+        40.0,  // OP_KICK_DRIFT: W read, 2 x (psi read + write)
+        40.0,  // OP_KICK_DRIFT_VINV
+        40.0,  // OP_DRIFT_RHO: 2 x (psi read + write), W write
+        24.0,  // OP_RHO_FWD: 2 x psi read, W write
+        16.0,  // OP_FWD
+        16.0,  // OP_FWD_MUL_INV
+        16.0,  // OP_INV
+        40.0,  // OP_KICK_VINV: W read, 2 x (psi read + write)
+        40.0,  // OP_KICK_FWD_OUT: W read, 2 x (psi read + spectrum write)
+        48.0,  // OP_STEPS_1D: per pair and step if the fields streamed (they stay on chip)
+        16.0,  // OP_MUL_INV
+    };
+    if (launches) *launches = h->prof_launches[op];
+    if (total_ms) *total_ms = h->prof_ms[op];
+    if (bytes_per_cell) *bytes_per_cell = bpc[op];
+    if (fields_per_launch) *fields_per_launch = h->prof_fields[op];
+    if (cells) *cells = h->prof_cells[op];
+    return TWA_OK;
+}
+
+long long twa_last_launch_count(const twa_handle* h) { return h ? h->launches : 0; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner: for every pass of the FP32 pipelines, time each instantiated lines-per-CTA variant on
+// the handle's own buffers and keep the fastest.  Results are cached in a flat JSON object keyed by
+// "N,axis,op,dims" so later handles with the same shapes skip the timing.
+namespace {
+
+std::string tune_key(const Inst& I, int axis, int op) {
+    std::ostringstream s;
+    s << I.n[0] << "x" << I.n[1] << "x" << I.n[2] << ":slots" << I.n_slots << ":axis" << axis << ":op" << op;
+    return s.str();
+}
+
+std::map<std::string, int> read_cache(const char* path) {
+    std::map<std::string, int> m;
+    if (!path) return m;
+    std::ifstream f(path);
+    if (!f) return m;
+    std::string txt((std::istreambuf_iterator<char>(f)), std::istreambuf_iterator<char>());
+    size_t i = 0;
+    while ((i = txt.find('"', i)) != std::string::npos) {
+        const size_t j = txt.find('"', i + 1);
+        if (j == std::string::npos) break;
+        const std::string k = txt.substr(i + 1, j - i - 1);
+        const size_t c = txt.find(':', j);
+        if (c == std::string::npos) break;
+        m[k] = std::atoi(txt.c_str() + c + 1);
+        i = txt.find_first_of(",}", c);
+        if (i == std::string::npos) break;
+    }
+    return m;
+}
+
+void write_cache(const char* path, const std::map<std::string, int>& m) {
+    if (!path) return;
+    std::ofstream f(path);
+    f << "{\n";
+    size_t n = 0;
+    for (const auto& kv : m) f << "  \"" << kv.first << "\": " << kv.second << (++n < m.size() ? ",\n" : "\n");
+    f << "}\n";
+}
+
+}  // namespace
+
+extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!psi) return fail(h, TWA_EINVAL, "twa_autotune: null buffer");
+    if (h->p.precision != TWA_F32) return TWA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::map<std::string, int> cache = read_cache(cache_path);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512};
+    for (auto& I : h->in) {
+        float2* f = inst_psi(I, psi);
+        struct P {
+            int axis, op, fields;
+            float2* buf;
+            float2* out;
+        };
+        std::vector<P> passes;
+        const int Pn = I.n_pairs, Sn = I.n_slots;
+        if (I.mode == MODE_1D) {
+            passes = {{0, OP_STEPS_1D, Pn, I.vc, nullptr}};
+        } else if (I.mode == MODE_2D) {
+            passes = {{0, OP_KICK_DRIFT, Pn, I.vc, nullptr}, {1, OP_DRIFT_RHO, Pn, I.vc, nullptr},
+                      {0, OP_FWD_MUL_INV, Pn, I.vc, nullptr}, {1, OP_INV, Pn, I.vc, nullptr},
+                      {1, OP_RHO_FWD, Pn, I.vc, nullptr}};
+            if (I.spec) passes.push_back({1, OP_FWD, Sn, I.spec, nullptr});
+        } else {
+            passes = {{0, OP_KICK_DRIFT_VINV, Pn, I.vc, nullptr}, {1, OP_DRIFT, Sn, I.vc, nullptr},
+                      {2, OP_DRIFT_RHO, Pn, I.vc, nullptr}, {0, OP_FWD, Pn, I.vc, nullptr},
+                      {1, OP_FWD_MUL_INV, Pn, I.vc, nullptr}, {2, OP_INV, Pn, I.vc, nullptr},
+                      {2, OP_RHO_FWD, Pn, I.vc, nullptr}, {0, OP_INV, Pn, I.vc, nullptr},
+                      {0, OP_KICK_VINV, Pn, I.vc, nullptr}};
+            if (I.spec) {
+                passes.push_back({1, OP_FWD, Sn, I.spec, nullptr});
+                passes.push_back({2, OP_FWD, Sn, I.spec, nullptr});
+            }
+        }
+        for (const auto& ps : passes) {
+            const std::string key = tune_key(I, ps.axis, ps.op);
+            auto hit = cache.find(key);
+            if (hit != cache.end() && variant_ok(I.n[ps.axis], ps.op, ps.axis > 0, hit->second)) {
+                I.lines[key_of(ps.axis, ps.op)] = hit->second;
+                continue;
+            }
+            float best = 1e30f;
+            int best_l = 0;
+            for (int l : cand) {
+                if (!variant_ok(I.n[ps.axis], ps.op, ps.axis > 0, l)) continue;
+                if (ps.op != OP_STEPS_1D && ps.axis == 0 && l > I.cells / I.n[0]) continue;
+                const int ns = (ps.op == OP_STEPS_1D) ? 4 : 0;
+                RC(run_pass(h, I, f, ps.axis, ps.op, 0.0, ps.buf, ps.out, ps.fields, st, ns, l));
+                CU(cudaEventRecord(e0, st));
+                for (int r = 0; r < 3; ++r) RC(run_pass(h, I, f, ps.axis, ps.op, 0.0, ps.buf, ps.out, ps.fields, st, ns, l));
+                CU(cudaEventRecord(e1, st));
+                CU(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CU(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    best_l = l;
+                }
+            }
+            if (best_l) {
+                I.lines[key_of(ps.axis, ps.op)] = best_l;
+                cache[key] = best_l;
+            }
+        }
+        CU(cudaMemsetAsync(I.vc, 0, (size_t)I.n_pairs * I.cells * sizeof(float2), st));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    write_cache(cache_path, cache);
+    CU(cudaStreamSynchronize(st));
+    return TWA_OK;
+}

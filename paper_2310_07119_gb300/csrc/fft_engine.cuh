@@ -1,0 +1,222 @@
+// fft_engine.cuh - register-resident Stockham FFT of one line, exchanged through shared memory.
+//
+// The split-step of Sec. III.B.2 needs, per step and per field, forward and inverse FFTs along
+// every axis (kinetic factor) and the FFTs of the Poisson solve.  Each line of length N is held by
+// T = N / RMAX threads with RMAX complex values each in registers.  A transform is a sequence of
+// Stockham autosort stages (radix R_s, sub-transform length Ns = prod of earlier radices): every
+// butterfly j takes x[j + r N/R], multiplies by W_{Ns R}^{r (j mod Ns)}, does an in-register
+// radix-R DFT and lands at (j / Ns) Ns R + (j mod Ns) + r Ns.  Between stages the values are
+// exchanged through a padded shared-memory line (one extra float2 per 16 to avoid bank
+// conflicts).  The forward transform ends in the layout the inverse starts from, so a pointwise
+// operation in Fourier space between them (kinetic phase, Poisson multiplier) needs no data
+// movement.  All transforms are unnormalized; scale factors live in the pointwise tables.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace twa {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// a * (hi + lo) for a constant carried as a float pair hi + lo (lo = remainder of the exact value):
+// the small product a * lo enters the innermost fma, so the result carries the constant to about
+// twice float precision and every product is rounded once inside an fma.  Without this, the
+// rounding of the twiddle constants biases every transform the same way and the error of the
+// split step grows linearly in the number of steps.
+__device__ __forceinline__ float2 cmul_c(float2 a, float2 hi, float2 lo) {
+    const float lx = fmaf(a.x, lo.x, -a.y * lo.y);
+    const float ly = fmaf(a.x, lo.y, a.y * lo.x);
+    return make_float2(fmaf(a.x, hi.x, fmaf(-a.y, hi.y, lx)), fmaf(a.x, hi.y, fmaf(a.y, hi.x, ly)));
+}
+
+// cos and sin of 2 pi j / 32 (mathematical constants rounded to float).
+constexpr float kCos32[32] = {
+    1.f, 0.98078528040323043f, 0.92387953251128674f, 0.83146961230254524f, 0.70710678118654757f,
+    0.55557023301960229f, 0.38268343236508984f, 0.19509032201612833f, 0.f, -0.19509032201612819f,
+    -0.38268343236508973f, -0.55557023301960196f, -0.70710678118654746f, -0.83146961230254535f,
+    -0.92387953251128674f, -0.98078528040323043f, -1.f, -0.98078528040323043f, -0.92387953251128685f,
+    -0.83146961230254546f, -0.70710678118654768f, -0.55557023301960218f, -0.38268343236509034f,
+    -0.19509032201612866f, 0.f, 0.1950903220161283f, 0.38268343236509f, 0.55557023301960184f,
+    0.70710678118654735f, 0.83146961230254524f, 0.92387953251128652f, 0.98078528040323032f};
+constexpr float kSin32[32] = {
+    0.f, 0.19509032201612825f, 0.38268343236508978f, 0.55557023301960218f, 0.70710678118654746f,
+    0.83146961230254524f, 0.92387953251128674f, 0.98078528040323043f, 1.f, 0.98078528040323043f,
+    0.92387953251128674f, 0.83146961230254546f, 0.70710678118654757f, 0.55557023301960218f,
+    0.38268343236508989f, 0.19509032201612861f, 0.f, -0.19509032201612836f, -0.38268343236508967f,
+    -0.55557023301960196f, -0.70710678118654746f, -0.83146961230254524f, -0.92387953251128652f,
+    -0.98078528040323032f, -1.f, -0.98078528040323043f, -0.92387953251128663f, -0.83146961230254546f,
+    -0.70710678118654768f, -0.55557023301960218f, -0.38268343236509039f, -0.19509032201612872f};
+
+// cos(2 pi j / 32) - kCos32[j] and sin(2 pi j / 32) - kSin32[j], rounded to float.
+constexpr float kCos32Lo[32] = {0.000000000e+00f, 2.973947311e-08f, 2.830749035e-08f, 1.687026374e-08f, 1.210161715e-08f, -1.176952125e-08f, 6.223350946e-09f, -1.670471400e-09f, 0.000000000e+00f, 1.670471539e-09f, -6.223350835e-09f, 1.176952158e-08f, -1.210161704e-08f, -1.687026385e-08f, -2.830749035e-08f, -2.973947311e-08f, 0.000000000e+00f, -2.973947311e-08f, -2.830749046e-08f, -1.687026396e-08f, -1.210161726e-08f, 1.176952136e-08f, -6.223351445e-09f, 1.670471067e-09f, 0.000000000e+00f, -1.670471428e-09f, 6.223351112e-09f, -1.176952169e-08f, 1.210161693e-08f, 1.687026374e-08f, 2.830749013e-08f, 2.973947300e-08f};
+constexpr float kSin32Lo[32] = {0.000000000e+00f, -1.670471483e-09f, 6.223350890e-09f, -1.176952136e-08f, 1.210161704e-08f, 1.687026374e-08f, 2.830749035e-08f, 2.973947311e-08f, 0.000000000e+00f, 2.973947311e-08f, 2.830749035e-08f, 1.687026396e-08f, 1.210161715e-08f, -1.176952136e-08f, 6.223351001e-09f, -1.670471123e-09f, 0.000000000e+00f, 1.670471372e-09f, -6.223350779e-09f, 1.176952158e-08f, -1.210161704e-08f, -1.687026374e-08f, -2.830749013e-08f, -2.973947300e-08f, 0.000000000e+00f, -2.973947311e-08f, -2.830749024e-08f, -1.687026396e-08f, -1.210161726e-08f, 1.176952136e-08f, -6.223351501e-09f, 1.670471012e-09f};
+
+// a * W_R^K with W_R = exp(-2 pi i / R) (forward) or exp(+2 pi i / R) (inverse); R | 32.
+template <int K, int R, bool INV>
+__device__ __forceinline__ float2 twc(float2 a) {
+    constexpr int J = (K * (32 / R)) % 32;
+    if constexpr (J == 0) {
+        return a;
+    } else if constexpr (J == 8) {  // -i forward, +i inverse
+        return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    } else if constexpr (J == 16) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (J == 24) {
+        return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    } else {
+        constexpr float c = kCos32[J], cl = kCos32Lo[J];
+        constexpr float s = INV ? kSin32[J] : -kSin32[J];
+        constexpr float sl = INV ? kSin32Lo[J] : -kSin32Lo[J];
+        return cmul_c(a, make_float2(c, s), make_float2(cl, sl));
+    }
+}
+
+template <int R, bool INV, int K = 0>
+struct Combine {
+    __device__ __forceinline__ static void run(float2* v, const float2* e, const float2* o) {
+        if constexpr (K < R / 2) {
+            const float2 t = twc<K, R, INV>(o[K]);
+            v[K] = cadd(e[K], t);
+            v[K + R / 2] = csub(e[K], t);
+            Combine<R, INV, K + 1>::run(v, e, o);
+        }
+    }
+};
+
+// In-register radix-R DFT (R = 2..32), natural order in and out, by even/odd splitting.
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v) {
+    if constexpr (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R > 2) {
+        float2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        dft<R / 2, INV>(e);
+        dft<R / 2, INV>(o);
+        Combine<R, INV>::run(v, e, o);
+    }
+}
+
+// Stage plans: radices in forward order, RMAX values per thread, T = N / RMAX threads per line.
+template <int N> struct Plan;
+#define TWA_PLAN(N_, RMAX_, S_, ...)                                   \
+    template <> struct Plan<N_> {                                      \
+        static constexpr int RMAX = RMAX_, S = S_, T = N_ / RMAX_;     \
+        static constexpr int R[S_] = {__VA_ARGS__};                    \
+    };
+TWA_PLAN(8, 8, 1, 8)
+TWA_PLAN(16, 16, 1, 16)
+TWA_PLAN(32, 16, 2, 16, 2)
+TWA_PLAN(64, 8, 2, 8, 8)
+TWA_PLAN(128, 16, 2, 16, 8)
+TWA_PLAN(256, 16, 2, 16, 16)
+TWA_PLAN(512, 16, 3, 16, 8, 4)
+TWA_PLAN(1024, 16, 3, 16, 16, 4)
+TWA_PLAN(2048, 16, 3, 16, 16, 8)
+#undef TWA_PLAN
+
+__host__ __device__ constexpr int pad_idx(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int line_stride(int n) { return (pad_idx(n) & 1) ? pad_idx(n) : pad_idx(n) + 1; }
+
+template <int N, bool INV, int s>
+struct StageInfo {
+    using P = Plan<N>;
+    static constexpr int R = INV ? P::R[P::S - 1 - s] : P::R[s];
+    static constexpr int NS = StageInfo<N, INV, s - 1>::NS * StageInfo<N, INV, s - 1>::R;
+};
+template <int N, bool INV>
+struct StageInfo<N, INV, 0> {
+    using P = Plan<N>;
+    static constexpr int R = INV ? P::R[P::S - 1] : P::R[0];
+    static constexpr int NS = 1;
+};
+
+// Position along the line of register slot `slot` in the natural layout (forward input,
+// inverse output) and in the spectral layout (forward output, inverse input).
+template <int N>
+__device__ __forceinline__ int pos_nat(int t, int slot) {
+    using P = Plan<N>;
+    constexpr int R0 = P::R[0];
+    return t + P::T * (slot / R0) + (slot % R0) * (N / R0);
+}
+template <int N>
+__device__ __forceinline__ int pos_spec(int t, int slot) {
+    using P = Plan<N>;
+    constexpr int RL = P::R[P::S - 1];
+    return t + P::T * (slot / RL) + (slot % RL) * (N / RL);
+}
+
+// WARP: every line lies inside one warp (T <= 32, contiguous lanes); MASK names the lanes that
+// exist in a CTA smaller than a warp.
+template <bool WARP, unsigned MASK>
+__device__ __forceinline__ void line_sync() {
+    if constexpr (WARP) __syncwarp(MASK);
+    else __syncthreads();
+}
+
+template <int N, bool INV, int s, bool WARP, unsigned MASK>
+struct FftStage {
+    using P = Plan<N>;
+    static constexpr int RMAX = P::RMAX, T = P::T, S = P::S;
+    using SI = StageInfo<N, INV, s>;
+    static constexpr int R = SI::R, NS = SI::NS;
+
+    __device__ __forceinline__ static void run(float2 (&v)[RMAX], int t, float2* sm, const float4* __restrict__ tw) {
+        constexpr int B = RMAX / R;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int j = t + T * b;
+            if constexpr (NS > 1) {
+                const int k = j & (NS - 1);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float4 w = __ldg(&tw[(r * k) * (N / (NS * R))]);
+                    v[b * R + r] = INV ? cmul_c(v[b * R + r], make_float2(w.x, -w.y), make_float2(w.z, -w.w))
+                                       : cmul_c(v[b * R + r], make_float2(w.x, w.y), make_float2(w.z, w.w));
+                }
+            }
+            dft<R, INV>(&v[b * R]);
+        }
+        if constexpr (s + 1 < S) {
+            constexpr int R2 = StageInfo<N, INV, s + 1>::R;
+            constexpr int B2 = RMAX / R2;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int j = t + T * b;
+                const int base = (j / NS) * NS * R + (j & (NS - 1));
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[pad_idx(base + r * NS)] = v[b * R + r];
+            }
+            line_sync<WARP, MASK>();
+#pragma unroll
+            for (int b = 0; b < B2; ++b) {
+                const int j = t + T * b;
+#pragma unroll
+                for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pad_idx(j + r * (N / R2))];
+            }
+            line_sync<WARP, MASK>();
+            FftStage<N, INV, s + 1, WARP, MASK>::run(v, t, sm, tw);
+        }
+    }
+};
+
+// Forward (INV = false) or inverse transform of one line held as in pos_nat / pos_spec.
+template <int N, bool INV, bool WARP, unsigned MASK = 0xffffffffu>
+__device__ __forceinline__ void fft_line(float2 (&v)[Plan<N>::RMAX], int t, float2* sm, const float4* __restrict__ tw) {
+    FftStage<N, INV, 0, WARP, MASK>::run(v, t, sm, tw);
+}
+
+}  // namespace twa

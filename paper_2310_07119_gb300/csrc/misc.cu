@@ -1,0 +1,237 @@
+// misc.cu - sampling, kick, ensemble-moment and reduction kernels.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_engine.cuh"
+#include "kernels.h"
+#include "passes.cuh"
+#include "reduce.cuh"
+
+namespace twa {
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64 multiplies; the
+// key is bumped by the Weyl constants before every round after the first.
+__device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                              uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+}
+
+template <class T2>
+__device__ __forceinline__ T2 make_c(double x, double y);
+template <>
+__device__ __forceinline__ float2 make_c<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+template <>
+__device__ __forceinline__ double2 make_c<double2>(double x, double y) { return make_double2(x, y); }
+
+// Eq. sample: slot 0 <- psi_cl; slot s >= 1 <- psi_cl + sigma (zR + i zI), zR, zI from Box-Muller
+// on the first two Philox words of counter (cell, s, instance, 0), key = seed; arithmetic in FP64.
+template <class T2>
+__global__ void k_sample(const double2* __restrict__ psi_cl, T2* __restrict__ psi, long long cells,
+                         int n_slots, uint32_t k0, uint32_t k1, uint32_t inst, double sigma) {
+    const long long total = cells * n_slots;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int slot = (int)(idx / cells);
+        const long long g = idx - (long long)slot * cells;
+        double2 z = psi_cl[g];
+        if (slot > 0) {
+            uint32_t c0 = (uint32_t)g, c1 = (uint32_t)slot, c2 = inst, c3 = 0;
+            philox4x32_10(c0, c1, c2, c3, k0, k1);
+            const double u0 = ((double)c0 + 0.5) * (1.0 / 4294967296.0);
+            const double u1 = ((double)c1 + 0.5) * (1.0 / 4294967296.0);
+            const double r = sqrt(-2.0 * log(u0));
+            double s, c;
+            sincospi(2.0 * u1, &s, &c);
+            z.x += sigma * (r * c);
+            z.y += sigma * (r * s);
+        }
+        psi[idx] = make_c<T2>(z.x, z.y);
+    }
+}
+
+// psi_s <- psi_s exp(-i kick V_s) for every slot, V of pair p packed in buf[p] (re: slot 2p, im: 2p+1).
+__global__ void k_kick_pairs(float2* __restrict__ psi, const float2* __restrict__ buf, long long cells,
+                             int n_slots, float kick, float kick_lo) {
+    const long long total = cells * n_slots;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int slot = (int)(idx / cells);
+        const long long g = idx - (long long)slot * cells;
+        const float2 c = buf[(long long)(slot >> 1) * cells + g];
+        psi[idx] = kick_w(psi[idx], kick, kick_lo, (slot & 1) ? c.y : c.x);
+    }
+}
+
+// Position-space moments (Eq. E[op], Eq. Q) of one instance, one thread per cell, streams summed
+// in slot order in FP64.  The pending half kick (kick = dt / (2 hbar), or 0) is applied on the fly
+// to the mean field; |psi|^2 does not depend on it.
+__global__ void k_moments_real(const float2* __restrict__ psi, const float2* __restrict__ buf,
+                               long long cells, int n_slots, float kick, float kick_lo, double inv_ns, double weyl,
+                               double* rho_mean, double* psi_mean, double* rho_cl, double* part) {
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v[NP_REAL] = {0, 0, 0, 0, 0, 0};
+    if (g < cells) {
+        double m2 = 0.0, pr = 0.0, pi = 0.0, bad = 0.0;
+        for (int s = 1; s < n_slots; ++s) {
+            const float2 z = psi[(long long)s * cells + g];
+            float2 zk = z;
+            if (kick != 0.f) {
+                const float2 c = buf[(long long)(s >> 1) * cells + g];
+                zk = kick_w(z, kick, kick_lo, (s & 1) ? c.y : c.x);
+            }
+            if (!isfinite(z.x) || !isfinite(z.y)) bad += 1.0;
+            m2 += (double)z.x * z.x + (double)z.y * z.y;
+            pr += zk.x;
+            pi += zk.y;
+        }
+        const float2 z0 = psi[g];
+        const double cl = (double)z0.x * z0.x + (double)z0.y * z0.y;
+        m2 *= inv_ns;
+        pr *= inv_ns;
+        pi *= inv_ns;
+        const double rm = m2 - weyl;
+        if (rho_mean) rho_mean[g] = rm;
+        if (psi_mean) {
+            psi_mean[2 * g] = pr;
+            psi_mean[2 * g + 1] = pi;
+        }
+        if (rho_cl) rho_cl[g] = cl;
+        if (!isfinite(z0.x) || !isfinite(z0.y)) bad += 1.0;
+        v[0] = m2 - (pr * pr + pi * pi);
+        v[1] = (rm - cl) * (rm - cl);
+        v[2] = cl * cl;
+        v[3] = m2;
+        v[4] = cl;
+        v[5] = bad;
+    }
+    block_reduce_store<NP_REAL>(v, part);
+}
+
+// Per-mode moments: a_k = sqrt(n dV / M) FFT(psi_s)_k (spec holds FFT(psi_s) for every slot).
+__global__ void k_moments_modes(const float2* __restrict__ spec, long long cells, int n_slots, double anorm2,
+                                double inv_ns, double* nk_mean, double* nk_var, double* part) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v[NP_MODES] = {0, 0};
+    if (k < cells) {
+        double a2s = 0.0, a4s = 0.0;
+        for (int s = 1; s < n_slots; ++s) {
+            const float2 z = spec[(long long)s * cells + k];
+            const double a2 = anorm2 * ((double)z.x * z.x + (double)z.y * z.y);
+            a2s += a2;
+            a4s += a2 * a2;
+        }
+        const double m2 = a2s * inv_ns, m4 = a4s * inv_ns;
+        const double nk = m2 - 0.5;
+        if (nk_mean) nk_mean[k] = nk;
+        if (nk_var) nk_var[k] = m4 - m2 - nk * nk;
+        v[0] = nk;
+    }
+    block_reduce_store<NP_MODES>(v, part);
+}
+
+// Sum the per-block partials in block order and form the TWA_NSCALARS scalars of one instance.
+__global__ void k_finish_scalars(const double* __restrict__ part_r, int nb_r, const double* __restrict__ part_m,
+                                 int nb_m, double dV, double q_offset, double* scalars, int* err_word) {
+    __shared__ double red[NP_REAL + NP_MODES][256];
+    double v[NP_REAL + NP_MODES];
+#pragma unroll
+    for (int j = 0; j < NP_REAL + NP_MODES; ++j) v[j] = 0.0;
+    for (int b = threadIdx.x; b < nb_r; b += 256)
+        for (int j = 0; j < NP_REAL; ++j) v[j] += part_r[(long long)b * NP_REAL + j];
+    for (int b = threadIdx.x; b < nb_m; b += 256)
+        for (int j = 0; j < NP_MODES; ++j) v[NP_REAL + j] += part_m[(long long)b * NP_MODES + j];
+    for (int j = 0; j < NP_REAL + NP_MODES; ++j) red[j][threadIdx.x] = v[j];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int j = 0; j < NP_REAL + NP_MODES; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double q = red[0][0] * dV - q_offset;
+        const double d2 = sqrt(red[1][0]), c2 = sqrt(red[2][0]);
+        scalars[0] = q;
+        scalars[1] = d2 / c2;
+        scalars[2] = red[3][0] * dV;
+        scalars[3] = red[4][0] * dV;
+        scalars[4] = red[5][0];
+        scalars[5] = (nb_m > 0) ? red[NP_REAL][0] : 0.0;
+        scalars[6] = d2;
+        scalars[7] = c2;
+        if (red[5][0] > 0.0 && err_word) atomicOr(err_word, 1);
+    }
+}
+
+// Copy the current output's scalars into series[counter] and advance the device counter (keeps a
+// captured graph identical across replays).
+__global__ void k_store_series(const double* __restrict__ cur, double* series, int* counter, int n) {
+    const int o = *counter;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) series[(long long)o * n + j] = cur[j];
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = o + 1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host launchers.
+int launch_sample_f32(const double2* psi_cl, float2* psi, long long cells, int n_slots, uint64_t seed,
+                      int inst, double sigma, cudaStream_t st) {
+    const long long total = cells * n_slots;
+    const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+    k_sample<float2><<<blocks, 256, 0, st>>>(psi_cl, psi, cells, n_slots, (uint32_t)seed,
+                                             (uint32_t)(seed >> 32), (uint32_t)inst, sigma);
+    return 0;
+}
+int launch_sample_f64(const double2* psi_cl, double2* psi, long long cells, int n_slots, uint64_t seed,
+                      int inst, double sigma, cudaStream_t st) {
+    const long long total = cells * n_slots;
+    const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+    k_sample<double2><<<blocks, 256, 0, st>>>(psi_cl, psi, cells, n_slots, (uint32_t)seed,
+                                              (uint32_t)(seed >> 32), (uint32_t)inst, sigma);
+    return 0;
+}
+int launch_kick_pairs(float2* psi, const float2* buf, long long cells, int n_slots, float kick, float kick_lo,
+                      cudaStream_t st) {
+    const long long total = cells * n_slots;
+    const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    k_kick_pairs<<<blocks, 256, 0, st>>>(psi, buf, cells, n_slots, kick, kick_lo);
+    return 0;
+}
+int moments_blocks(long long cells) { return (int)((cells + 255) / 256); }
+int launch_moments_real(const float2* psi, const float2* buf, long long cells, int n_slots, float kick,
+                        float kick_lo, double inv_ns, double weyl, double* rho_mean, double* psi_mean, double* rho_cl,
+                        double* part, cudaStream_t st) {
+    k_moments_real<<<moments_blocks(cells), 256, 0, st>>>(psi, buf, cells, n_slots, kick, kick_lo, inv_ns, weyl,
+                                                          rho_mean, psi_mean, rho_cl, part);
+    return 0;
+}
+int launch_moments_modes(const float2* spec, long long cells, int n_slots, double anorm2, double inv_ns,
+                         double* nk_mean, double* nk_var, double* part, cudaStream_t st) {
+    k_moments_modes<<<moments_blocks(cells), 256, 0, st>>>(spec, cells, n_slots, anorm2, inv_ns, nk_mean,
+                                                           nk_var, part);
+    return 0;
+}
+int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, int nb_m, double dV,
+                          double q_offset, double* scalars, int* err_word, cudaStream_t st) {
+    k_finish_scalars<<<1, 256, 0, st>>>(part_r, nb_r, part_m, nb_m, dV, q_offset, scalars, err_word);
+    return 0;
+}
+int launch_store_series(const double* cur, double* series, int* counter, int n, cudaStream_t st) {
+    k_store_series<<<1, 128, 0, st>>>(cur, series, counter, n);
+    return 0;
+}
+
+}  // namespace twa

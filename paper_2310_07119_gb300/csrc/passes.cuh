@@ -1,0 +1,312 @@
+// passes.cuh - fused FP32 line passes of the batched split step (Sec. III.B.2).
+//
+// A pass transforms every line of a field along one axis.  A CTA owns LINES lines: for the x axis
+// (contiguous, "row" passes) LINES consecutive rows, for y and z (strided, "column" passes) LINES
+// lines whose starting cells are consecutive in memory, so that a warp reads 32 consecutive
+// complex values per access.  The pointwise work of the method is fused into the passes:
+//   kick      psi <- psi exp(-i kick V)            (U^V, kick = a dt / hbar, a = 1/2 or 1)
+//   drift     FFT -> exp(-i hbar k_a^2 dt / 2) / N_a -> iFFT along the axis (U^T factorizes by axis)
+//   density   rho = |psi|^2 of two streams packed as one complex line c = rho_0 + i rho_1, so one
+//             complex transform serves two real Poisson solves
+//   Poisson   W_k = rho_k / k^2, W_0 = 0, applied between the last forward and the first inverse
+//             transform; the potential of lap V = C (rho - mean rho) (Eq. mft_normed) is V = -C W / cells,
+//             and that scale is folded into the kick factor (kick = -a dt C / (hbar cells), carried as a
+//             float hi + lo pair so its rounding does not bias every step by the same amount)
+// Fields of the batch are processed in pairs of slots (2p, 2p+1) that share one packed Poisson
+// line in `buf`; a missing partner (odd slot count) contributes zero density.
+#pragma once
+#include "fft_engine.cuh"
+
+namespace twa {
+
+enum Op : int {
+    OP_DRIFT = 0,        // one field of psi: fwd, kinetic phase, inv
+    OP_KICK_DRIFT,       // pair, V real in buf: kick both slots, drift both
+    OP_KICK_DRIFT_VINV,  // pair, buf spectral along this axis: inverse -> V, kick, drift
+    OP_DRIFT_RHO,        // pair: drift both slots, packed density -> forward -> buf (spectral)
+    OP_RHO_FWD,          // pair: packed density of psi -> forward -> buf
+    OP_FWD,              // one field of buf: forward (natural -> spectral layout)
+    OP_FWD_MUL_INV,      // one field of buf: forward, Poisson multiplier, inverse
+    OP_INV,              // one field of buf: inverse (spectral -> natural layout)
+    OP_KICK_VINV,        // pair, buf spectral: inverse -> V, kick both slots (no drift)
+    OP_KICK_FWD_OUT,     // pair, V real in buf: kick both slots, forward into out (moments)
+    OP_STEPS_1D,         // pair, 1D field = one line: nsteps whole steps on chip
+    OP_MUL_INV,          // one field of buf (spectral): Poisson multiplier, inverse
+    OP_COUNT
+};
+
+struct PassArgs {
+    float2* psi;            // slot 0 of the instance
+    float2* buf;            // packed Poisson buffer (one field per pair) or a field buffer
+    float2* out;            // destination of OP_KICK_FWD_OUT (one field per slot)
+    const float4* tw;       // exp(-2 pi i m / N), m < N, as (hi.re, hi.im, lo.re, lo.im)
+    const float2* ph;       // exp(-i hbar k^2 dt / 2) / N along this axis, FFT order (float hi part)
+    const float2* ph_lo;    // the remainder (exact value - hi) rounded to float
+    const float* k2x;       // k^2 tables per axis (FFT order; length 1 and 0 for unused axes)
+    const float* k2y;
+    const float* k2z;
+    float kick, kick_lo;    // -a dt C / (hbar cells) for the (first) kick, as hi + lo
+    float kick2, kick2_lo;  // same with a = 1 for later kicks (OP_STEPS_1D)
+    int S;                  // stride of the axis (elements)
+    int Qn;                 // strided: starting cells per outer index; contiguous: unused
+    long long OS;           // strided: outer stride
+    long long cells;
+    int n_slots;
+    int n_pairs;
+    int lx, lxy;            // log2 nx, log2 (nx ny)
+    int nsteps;             // OP_STEPS_1D
+    float post;             // OP_FWD: factor applied before the store (1, or 1/N to undo an inverse)
+};
+
+// z * exp(-i theta), theta reduced to [-pi, pi] by a two-constant (Cody-Waite) split of 2 pi.
+__device__ __forceinline__ float2 kick_phase(float2 z, float theta) {
+    const float n = rintf(theta * 0.15915494309189535f);
+    float r = fmaf(-n, 6.28125f, theta);
+    r = fmaf(-n, 0.0019353071795862327f, r);
+    float s, c;
+    sincosf(r, &s, &c);
+    return make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
+}
+
+// z * exp(-i (k_hi + k_lo) W): the kick with its scale carried in two floats.
+__device__ __forceinline__ float2 kick_w(float2 z, float k_hi, float k_lo, float W) {
+    return kick_phase(z, fmaf(k_hi, W, k_lo * W));
+}
+
+template <int N, int LINES, bool STRIDED, int OP>
+__global__ void __launch_bounds__(LINES * Plan<N>::T)
+k_line(const PassArgs a) {
+    using P = Plan<N>;
+    constexpr int T = P::T, RMAX = P::RMAX, LS = line_stride(N);
+    constexpr bool WARP = !STRIDED && (T <= 32);
+    constexpr unsigned MASK = (LINES * T >= 32) ? 0xffffffffu : ((1u << (LINES * T)) - 1u);
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x;
+    const int l = STRIDED ? (tid % LINES) : (tid / T);
+    const int t = STRIDED ? (tid / LINES) : (tid % T);
+    float2* sm = smem + l * LS;
+    const float4* __restrict__ tw = a.tw;
+
+    // Line of this thread; lines past the end of the field (partial tiles of small grids) run on a
+    // clamped valid line and store nothing, so every thread reaches every barrier.
+    long long base;
+    bool act;
+    if constexpr (STRIDED) {
+        const int tq = (a.Qn + LINES - 1) / LINES;
+        const int q = (int)(blockIdx.x % tq) * LINES + l;
+        act = q < a.Qn;
+        base = (long long)(act ? q : a.Qn - 1) + (long long)(blockIdx.x / tq) * a.OS;
+    } else {
+        const long long rows = a.cells / N;
+        const long long row = (long long)blockIdx.x * LINES + l;
+        act = row < rows;
+        base = (act ? row : rows - 1) * N;
+    }
+    const long long S = STRIDED ? a.S : 1;
+    const int f = blockIdx.y;
+    float2 v[RMAX];
+
+    auto load_nat = [&](float2 (&w)[RMAX], const float2* F) {
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) w[i] = F[base + pos_nat<N>(t, i) * S];
+    };
+    auto store_nat = [&](const float2 (&w)[RMAX], float2* F) {
+        if (!act) return;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) F[base + pos_nat<N>(t, i) * S] = w[i];
+    };
+    auto load_spec = [&](float2 (&w)[RMAX], const float2* F) {
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) w[i] = F[base + pos_spec<N>(t, i) * S];
+    };
+    auto store_spec = [&](const float2 (&w)[RMAX], float2* F) {
+        if (!act) return;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) F[base + pos_spec<N>(t, i) * S] = w[i];
+    };
+    // multiply by the kinetic phase carried as hi + lo, so its rounding does not repeat every step
+    auto phase = [&](float2 (&w)[RMAX]) {
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+            const int k = pos_spec<N>(t, i);
+            w[i] = cmul_c(w[i], __ldg(&a.ph[k]), __ldg(&a.ph_lo[k]));
+        }
+    };
+    auto poisson = [&](float2 (&w)[RMAX]) {
+        const int mx = (1 << a.lx) - 1, my = (1 << (a.lxy - a.lx)) - 1;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+            const long long e = base + pos_spec<N>(t, i) * S;
+            const float k2 = __ldg(&a.k2x[e & mx]) + __ldg(&a.k2y[(e >> a.lx) & my]) + __ldg(&a.k2z[e >> a.lxy]);
+            const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
+            w[i] = make_float2(w[i].x * m, w[i].y * m);
+        }
+    };
+    auto drift = [&](float2 (&w)[RMAX]) {
+        fft_line<N, false, WARP, MASK>(w, t, sm, tw);
+        phase(w);
+        fft_line<N, true, WARP, MASK>(w, t, sm, tw);
+    };
+
+    if constexpr (OP == OP_DRIFT) {
+        float2* F = a.psi + (long long)f * a.cells;
+        load_nat(v, F);
+        drift(v);
+        store_nat(v, F);
+    } else if constexpr (OP == OP_KICK_DRIFT || OP == OP_KICK_FWD_OUT) {
+        const float2* VC = a.buf + (long long)f * a.cells;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int slot = 2 * f + h;
+            if (slot >= a.n_slots) break;
+            float2* F = a.psi + (long long)slot * a.cells;
+            if (a.kick != 0.f) {
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) {
+                    const long long e = base + pos_nat<N>(t, i) * S;
+                    const float2 c = VC[e];
+                    v[i] = kick_w(F[e], a.kick, a.kick_lo, h ? c.y : c.x);
+                }
+            } else {
+                load_nat(v, F);
+            }
+            if constexpr (OP == OP_KICK_DRIFT) {
+                drift(v);
+                store_nat(v, F);
+            } else {
+                fft_line<N, false, WARP, MASK>(v, t, sm, tw);
+                store_spec(v, a.out + (long long)slot * a.cells);
+            }
+        }
+    } else if constexpr (OP == OP_KICK_DRIFT_VINV || OP == OP_KICK_VINV) {
+        float2 w[RMAX];
+        load_spec(w, a.buf + (long long)f * a.cells);
+        fft_line<N, true, WARP, MASK>(w, t, sm, tw);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int slot = 2 * f + h;
+            if (slot >= a.n_slots) break;
+            float2* F = a.psi + (long long)slot * a.cells;
+            load_nat(v, F);
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, h ? w[i].y : w[i].x);
+            if constexpr (OP == OP_KICK_DRIFT_VINV) drift(v);
+            store_nat(v, F);
+        }
+    } else if constexpr (OP == OP_DRIFT_RHO || OP == OP_RHO_FWD) {
+        float2 c[RMAX];
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int slot = 2 * f + h;
+            if (slot < a.n_slots) {
+                float2* F = a.psi + (long long)slot * a.cells;
+                load_nat(v, F);
+                if constexpr (OP == OP_DRIFT_RHO) {
+                    drift(v);
+                    store_nat(v, F);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) v[i] = make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) {
+                const float r2 = fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
+                if (h == 0) c[i].x = r2; else c[i].y = r2;
+            }
+        }
+        fft_line<N, false, WARP, MASK>(c, t, sm, tw);
+        store_spec(c, a.buf + (long long)f * a.cells);
+    } else if constexpr (OP == OP_FWD) {
+        float2* F = a.buf + (long long)f * a.cells;
+        load_nat(v, F);
+        fft_line<N, false, WARP, MASK>(v, t, sm, tw);
+        if (a.post != 1.0f) {
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) v[i] = make_float2(v[i].x * a.post, v[i].y * a.post);
+        }
+        store_spec(v, F);
+    } else if constexpr (OP == OP_FWD_MUL_INV) {
+        float2* F = a.buf + (long long)f * a.cells;
+        load_nat(v, F);
+        fft_line<N, false, WARP, MASK>(v, t, sm, tw);
+        poisson(v);
+        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+        store_nat(v, F);
+    } else if constexpr (OP == OP_MUL_INV) {
+        float2* F = a.buf + (long long)f * a.cells;
+        load_spec(v, F);
+        poisson(v);
+        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+        store_nat(v, F);
+    } else if constexpr (OP == OP_INV) {
+        float2* F = a.buf + (long long)f * a.cells;
+        load_spec(v, F);
+        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+        store_nat(v, F);
+    } else if constexpr (OP == OP_STEPS_1D) {
+        // base is the line offset inside the field; here each line slot of the CTA is one pair.
+        const int p = (int)blockIdx.x * LINES + l;
+        const bool active = p < a.n_pairs;
+        const int pe = active ? p : a.n_pairs - 1;
+        const bool has1 = 2 * pe + 1 < a.n_slots;
+        float2* F0 = a.psi + (long long)(2 * pe) * a.cells;
+        float2* F1 = a.psi + (long long)(2 * pe + 1) * a.cells;
+        float2* VC = a.buf + (long long)pe * a.cells;
+        float2 u1[RMAX], w[RMAX];
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+            const int e = pos_nat<N>(t, i);
+            v[i] = F0[e];
+            u1[i] = has1 ? F1[e] : make_float2(0.f, 0.f);
+            w[i] = VC[e];
+        }
+#pragma unroll 1
+        for (int st = 0; st < a.nsteps; ++st) {
+            const float kk = (st == 0) ? a.kick : a.kick2;
+            const float kl = (st == 0) ? a.kick_lo : a.kick2_lo;
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) {
+                v[i] = kick_w(v[i], kk, kl, w[i].x);
+                u1[i] = kick_w(u1[i], kk, kl, w[i].y);
+            }
+            drift(v);
+            drift(u1);
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i)
+                w[i] = make_float2(fmaf(v[i].x, v[i].x, v[i].y * v[i].y), fmaf(u1[i].x, u1[i].x, u1[i].y * u1[i].y));
+            fft_line<N, false, WARP, MASK>(w, t, sm, tw);
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) {
+                const float k2 = __ldg(&a.k2x[pos_spec<N>(t, i)]);
+                const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
+                w[i] = make_float2(w[i].x * m, w[i].y * m);
+            }
+            fft_line<N, true, WARP, MASK>(w, t, sm, tw);
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) {
+                const int e = pos_nat<N>(t, i);
+                F0[e] = v[i];
+                if (has1) F1[e] = u1[i];
+                VC[e] = w[i];
+            }
+        }
+    }
+}
+
+// Host-side launcher of one pass (defined per N in passes_n*.cu).
+struct LaunchCfg {
+    int op;
+    bool strided;
+    int lines;
+    dim3 grid;
+};
+template <int N>
+int launch_line(const LaunchCfg& c, const PassArgs& a, cudaStream_t st, bool prepare_only);
+template <int N>
+bool has_variant(int op, bool strided, int lines);
+int plan_threads_per_line(int n);
+
+}  // namespace twa

@@ -1,0 +1,266 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 batched path): the field relative L2 error per realization
+must stay <= 1e-4 after 100 steps; <rho> <= 1e-5 relative; the correction norm
+<= 1% relative.  FP32 storage rounds every value to 6e-8 relative and each
+transform adds O(log2 N) such roundings, so the per-step field error is a few
+1e-7 and 100 steps stay well inside 1e-4 for these non-chaotic intervals.  The
+FP64 plain path is held to 1e-10 (rounding of the same arithmetic in FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import twa_inputs as ti
+from oracle import sp, twa
+from tests.gpu_common import field_rel_l2, make_ensemble, oracle_batch
+
+pytestmark = pytest.mark.gpu
+
+F32_FIELD_TOL = 1e-4
+RHO_TOL = 1e-5
+CORR_TOL = 1e-2
+
+
+# Time steps of the full-size workloads (pi/4 rule of the 128^3 and 256^3 grids, 256^2 for 2D),
+# so that per-step phases and the 100-step physical time match the measured configurations.
+DT_128 = ti.dt_pi4_rule(ti.Grid.cube(3, 128), ti.HBAR_3D)
+DT_256 = ti.dt_pi4_rule(ti.Grid.cube(3, 256), ti.HBAR_3D)
+DT_2D = ti.dt_pi4_rule(ti.Grid.cube(2, 256), ti.HBAR_3D)
+
+
+def _cases():
+    return {
+        "1d_bump256": ti.workload_1d_bump(256, 7, 100),
+        "1d_cosine64": ti.Workload("cosine", ti.Grid.cube(1, 64), ti.Physics(0.01, 4 * np.pi, 1e-3, 1e6), 4, 100, 10, 0, 3),
+        "2d_merger64": ti.small_workload("merger2d", 2, 64, 5, 100, n_tot=1e9, dt=DT_2D),
+        "3d_kgauss16": ti.small_workload("kgauss", 3, 16, 5, 100, n_tot=1e8, dt=DT_128),
+        "3d_kgauss32_pi4": ti.small_workload("kgauss", 3, 32, 3, 100, n_tot=1e8),
+        "3d_soliton32": ti.small_workload("soliton", 3, 32, 3, 100, n_tot=1e10, dt=DT_256),
+    }
+
+
+CASES = _cases()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sample_matches_oracle(precision):
+    w = ti.small_workload("kgauss", 3, 16, 4, 0, n_tot=1e6)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], precision)
+    ens.sample([cl], w.noise_seed)
+    got = ens.fields(0).cpu().numpy()
+    ref = twa.sample(cl, w.noise_seed, w.n_real, w.phys.n_tot, w.grid.dV)
+    if precision == 0:
+        # FP64 arithmetic rounded once to FP32
+        assert np.max(np.abs(got - ref.astype(np.complex64))) <= 2 * np.finfo(np.float32).eps * np.abs(ref).max()
+    else:
+        assert np.max(np.abs(got - ref)) < 1e-14 * np.abs(ref).max()
+    assert np.array_equal(got[0], ref[0].astype(got.dtype))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_f32_steps_match_oracle(name):
+    w = CASES[name]
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    ens.sample([cl], w.noise_seed)
+    ens.step(w.n_steps)
+    got = ens.fields(0).cpu().numpy().astype(np.complex128)
+    ref = oracle_batch(w, cl, w.n_steps)
+    err = field_rel_l2(got, ref, w.grid.dim)
+    assert np.all(err < F32_FIELD_TOL), err
+    # moments of the synchronized ensemble
+    m = ens.moments(0)
+    mo = twa.moments(ref, w.phys.n_tot, w.grid.L, w.grid.dim)
+    rm = m["rho_mean"].cpu().numpy().reshape(w.grid.shape)
+    assert np.linalg.norm(rm - mo["rho_mean"]) / np.linalg.norm(mo["rho_mean"]) < RHO_TOL
+    sc = m["scalars"].cpu().numpy()
+    assert abs(sc[1] - mo["corr"]) <= CORR_TOL * mo["corr"]
+    mass = sp.mass(ref, w.grid.dV, w.grid.dim)
+    assert abs(sc[2] - mass[1:].mean()) < 1e-5 * mass[1:].mean()     # noisy streams carry M/(2n) extra
+    assert abs(sc[3] - mass[0]) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["1d_bump256", "2d_merger64", "3d_kgauss16"])
+def test_f64_plain_path_matches_oracle(name):
+    w = CASES[name]
+    n = 20
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 1)
+    ens.sample([cl], w.noise_seed)
+    ens.step(n)
+    got = ens.fields(0).cpu().numpy()
+    ref = oracle_batch(w, cl, n)
+    assert np.all(field_rel_l2(got, ref, w.grid.dim) < 1e-10)
+    m = ens.moments(0)
+    mo = twa.moments(ref, w.phys.n_tot, w.grid.L, w.grid.dim)
+    for k in ("rho_mean", "rho_cl", "nk_mean"):
+        g = m[k].cpu().numpy().reshape(w.grid.shape)
+        assert np.max(np.abs(g - mo[k])) <= 1e-8 * np.max(np.abs(mo[k])) + 1e-10, k
+    # Var n_k = mean|a|^4 - mean|a|^2 - <n_k>^2 cancels terms of size <n_k>^2: FP64 rounding of those
+    g = m["nk_var"].cpu().numpy().reshape(w.grid.shape)
+    assert np.max(np.abs(g - mo["nk_var"])) <= 1e-13 * np.max(mo["nk_mean"]) ** 2 + 1e-8 * np.max(np.abs(mo["nk_var"]))
+    assert abs(m["scalars"][0].item() - mo["Q"]) < 1e-9 * max(1.0, abs(mo["Q"]))
+
+
+@pytest.mark.parametrize("name", ["2d_merger64", "3d_kgauss16", "1d_bump256"])
+def test_f32_moments_match_oracle(name):
+    w = CASES[name]
+    n = 30
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    ens.sample([cl], w.noise_seed)
+    ens.step(n)
+    m = ens.moments(0)
+    ref = oracle_batch(w, cl, n)
+    mo = twa.moments(ref, w.phys.n_tot, w.grid.L, w.grid.dim)
+    sh = w.grid.shape
+    pm = m["psi_mean"].cpu().numpy().reshape(sh + (2,))
+    pm = pm[..., 0] + 1j * pm[..., 1]
+    assert np.linalg.norm(pm - mo["psi_mean"]) / np.linalg.norm(mo["psi_mean"]) < 1e-5
+    assert np.linalg.norm(m["rho_cl"].cpu().numpy().reshape(sh) - mo["rho_cl"]) / np.linalg.norm(mo["rho_cl"]) < 1e-5
+    # an FP32 transform resolves |a_k|^2 to ~1e-6 of the total occupation n_tot: check the modes
+    # holding at least 1e-5 of it to 1e-3 relative, and all modes to 1e-6 n_tot absolute
+    nk = m["nk_mean"].cpu().numpy().reshape(sh)
+    tot = np.sum(mo["nk_mean"])
+    big = mo["nk_mean"] > 1e-5 * tot
+    assert np.max(np.abs(nk[big] - mo["nk_mean"][big]) / mo["nk_mean"][big]) < 1e-3
+    assert np.max(np.abs(nk - mo["nk_mean"])) < 1e-6 * tot
+    # Q is a small difference of large means: compare against the spread of the ensemble
+    sc = m["scalars"].cpu().numpy()
+    spread = np.sum(np.abs(ref[1:] - ref[1:].mean(0)) ** 2) / (w.n_real) * w.grid.dV
+    assert abs(sc[0] - mo["Q"]) < 2e-3 * spread
+    assert abs(sc[5] - np.sum(mo["nk_mean"])) < 1e-4 * np.sum(np.abs(mo["nk_mean"]))
+
+
+def test_run_series_matches_oracle():
+    w = ti.small_workload("kgauss", 3, 16, 6, 40, n_tot=1e8, out_every=10, dt=DT_128)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    series = ens.run([cl], w.noise_seed, w.n_steps, w.out_every).cpu().numpy()
+    t, ref_series, ref_final = twa.run(cl, w.phys.hbar_m, w.phys.C, w.phys.dt, w.grid.L, 3, w.phys.n_tot,
+                                       w.n_real, w.noise_seed, w.n_steps, w.out_every)
+    assert series.shape[0] == len(ref_series)
+    for o, mo in enumerate(ref_series):
+        assert abs(series[o, 0, 1] - mo["corr"]) <= CORR_TOL * mo["corr"] + 1e-12
+        assert abs(series[o, 0, 5] - np.sum(mo["nk_mean"])) < 1e-4 * np.sum(np.abs(mo["nk_mean"]))
+    got = ens.fields(0).cpu().numpy().astype(np.complex128)
+    assert np.all(field_rel_l2(got, ref_final, 3) < F32_FIELD_TOL)
+
+
+def test_run_is_bitwise_deterministic_and_replays_graph():
+    w = ti.small_workload("merger2d", 2, 64, 4, 30, n_tot=1e9, out_every=10, dt=DT_2D)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    s1 = ens.run([cl], w.noise_seed, w.n_steps, w.out_every).cpu().numpy()
+    f1 = ens.fields(0).cpu().numpy().copy()
+    s2 = ens.run([cl], w.noise_seed, w.n_steps, w.out_every).cpu().numpy()
+    f2 = ens.fields(0).cpu().numpy()
+    assert np.array_equal(s1, s2) and np.array_equal(f1, f2)
+
+
+def test_uneven_multi_instance_batch():
+    w1 = ti.small_workload("merger2d", 2, 64, 5, 20, n_tot=1e9, dt=DT_2D)
+    w2 = ti.small_workload("merger2d", 2, 32, 3, 20, n_tot=1e9, dt=DT_2D)
+    w2 = ti.Workload(w2.name, w2.grid, w1.phys, w2.n_real, w2.n_steps, w2.out_every, w2.psi_cl_seed, w1.noise_seed)
+    ens = make_ensemble([w1, w2], 0)
+    ens.sample([w1.psi_cl(), w2.psi_cl()], w1.noise_seed)
+    ens.step(20)
+    for i, w in enumerate((w1, w2)):
+        ref = oracle_batch(w, w.psi_cl(), 20, instance=i)
+        got = ens.fields(i).cpu().numpy().astype(np.complex128)
+        assert np.all(field_rel_l2(got, ref, 2) < F32_FIELD_TOL)
+
+
+def test_streams_are_independent_of_batch_size():
+    # slots keep their Poisson partner (2p, 2p+1) when the batch grows, so results are bitwise equal
+    base = ti.small_workload("kgauss", 3, 16, 3, 10, n_tot=1e8)
+    big = ti.Workload(base.name, base.grid, base.phys, 7, 10, 5, base.psi_cl_seed, base.noise_seed)
+    cl = base.psi_cl()
+    out = []
+    for w in (base, big):
+        ens = make_ensemble([w], 0)
+        ens.sample([cl], w.noise_seed)
+        ens.step(10)
+        out.append(ens.fields(0).cpu().numpy())
+    assert np.array_equal(out[0], out[1][:4])
+
+
+def test_nonfinite_input_is_flagged_and_contained_to_its_pair():
+    from paper_2310_07119_gb300 import twa_sync_status
+    w = ti.small_workload("merger2d", 2, 32, 5, 5, n_tot=1e9)
+    cl = w.psi_cl()
+    clean = make_ensemble([w], 0)
+    clean.sample([cl], w.noise_seed)
+    clean.step(5)
+    ens = make_ensemble([w], 0)
+    ens.sample([cl], w.noise_seed)
+    f = ens.fields(0)
+    f[3, 5, 7] = complex(float("nan"), 0.0)          # slot 3 (pair 1 = slots 2, 3)
+    ens.step(5)
+    m = ens.moments(0)
+    assert m["scalars"][4].item() > 0
+    assert twa_sync_status(ens.h) == -5
+    a, b = ens.fields(0).cpu().numpy(), clean.fields(0).cpu().numpy()
+    for s in (0, 1, 4, 5):
+        assert np.array_equal(a[s], b[s]), s
+    assert not np.all(np.isfinite(a[3]))
+
+
+def test_autotune_keeps_parity(tmp_path):
+    w = ti.small_workload("kgauss", 3, 32, 4, 20, n_tot=1e8, dt=DT_128)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    cache = str(tmp_path / "tune.json")
+    ens.autotune(cache)
+    assert open(cache).read().count("op") >= 6
+    ens.sample([cl], w.noise_seed)
+    ens.step(20)
+    got = ens.fields(0).cpu().numpy().astype(np.complex128)
+    assert np.all(field_rel_l2(got, oracle_batch(w, cl, 20), 3) < F32_FIELD_TOL)
+
+
+def test_bench_size_sampled_realizations():
+    """128^3 x 256 streams (the bench layout), 100 KDK steps: sampled streams vs the oracle.
+
+    The oracle evolves the classical field and two sampled streams (same Philox counters) for
+    the same 100 steps; field and per-stream density must meet the field (1e-4) and <rho>
+    (1e-5) tolerances, and every stream must conserve its mass.
+    """
+    w = ti.workload_3d_condensation(128, 256, 100)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0, want_modes=False)
+    ens.sample([cl], w.noise_seed)
+    f = ens.fields(0)
+    mass0 = (f.abs() ** 2).sum(dim=(1, 2, 3)).double().cpu().numpy() * w.grid.dV
+    ens.step(w.n_steps)
+    mass = (f.abs() ** 2).sum(dim=(1, 2, 3)).double().cpu().numpy() * w.grid.dV
+    assert np.all(np.abs(mass - mass0) < 1e-5 * mass0)          # unitarity of every stream
+    slots = [0, 137, 256]
+    sub = f[slots].cpu().numpy().astype(np.complex128)
+    del f, ens
+    torch.cuda.empty_cache()
+    sig = twa.noise_sigma(w.phys.n_tot, w.grid.dV)
+    from oracle.philox import wigner_normals
+    ref = np.empty((len(slots),) + cl.shape, dtype=np.complex128)
+    for i, s in enumerate(slots):
+        if s == 0:
+            ref[i] = cl
+        else:
+            zr, zi = wigner_normals(w.noise_seed, cl.size, s)
+            ref[i] = cl + sig * (zr + 1j * zi).reshape(cl.shape)
+    for _ in range(w.n_steps):
+        ref = sp.step(ref, w.phys.hbar_m, w.phys.C, w.phys.dt, 1.0, 3)
+    assert np.all(field_rel_l2(sub, ref, 3) < F32_FIELD_TOL)
+    r_got, r_ref = np.abs(sub) ** 2, np.abs(ref) ** 2
+    rho_err = np.sqrt(np.sum((r_got - r_ref) ** 2, axis=(1, 2, 3)) / np.sum(r_ref ** 2, axis=(1, 2, 3)))
+    assert np.all(rho_err < RHO_TOL), rho_err
