@@ -158,6 +158,24 @@ int twa_profile_enable(twa_handle* h, int on);
 int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_ms, double* bytes_per_cell,
                      long long* fields_per_launch, long long* cells);
 
+/* Allocation-free 1D step (no counterpart in the paper; an interface for callers that cannot
+   allocate device memory where they step: a process whose device memory is owned by its own pool,
+   a loop that must not risk an allocation failure or the synchronization cudaMalloc/cudaFree can
+   cause).  Same computation as twa_step_batch on a one-instance 1D FP32 handle with these grid and
+   params: psi is the caller's synchronized batch of n_real + 1 fields of grid->n[0] cells (float2,
+   slot 0 = classical field), advanced in place by n_steps KDK steps on `stream`.  No handle is
+   used: the Poisson buffer and the FFT and phase tables live in static device arrays of the
+   library (TWA_STATIC_SCRATCH_ELEMS complex values plus about 72 KB of tables), held by every GPU
+   that loads the library until the process exits.  The first call on a device looks up the device
+   addresses of those arrays (make that first call before any stream capture).  Every call
+   rebuilds the tables and the Poisson field; calls whose work overlaps on the GPU share the arrays
+   and race.  Errors: TWA_EINVAL when grid->dim != 1, precision != TWA_F32, n[0] is not a power of
+   two in [8, 2048], or (n_real + 2) / 2 * n[0] > TWA_STATIC_SCRATCH_ELEMS (message via
+   twa_last_error(NULL)); TWA_ECUDA on a CUDA failure. */
+#define TWA_STATIC_SCRATCH_ELEMS (1 << 19)
+int twa_step_batch_1d_static(const twa_grid* grid, const twa_params* p, int n_real, void* psi,
+                             int n_steps, void* stream);
+
 /* Block on `stream` and report device-side failures recorded since the last call
    (TWA_ENONFINITE) or TWA_OK.  Clears the device error word. */
 int twa_sync_status(twa_handle* h, void* stream);

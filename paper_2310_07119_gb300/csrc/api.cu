@@ -823,6 +823,13 @@ int twa_sync_status(twa_handle* h, void* stream) {
 
 const char* twa_last_error(const twa_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
+}  // extern "C"
+
+// Record a failure of a handle-free entry point, reported by twa_last_error(NULL).
+void twa_set_global_error(const std::string& msg) { g_create_error = msg; }
+
+extern "C" {
+
 int twa_profile_enable(twa_handle* h, int on) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     CU(cudaDeviceSynchronize());
