@@ -153,7 +153,7 @@ int twa_run(twa_handle* h, const void* psi_cl, uint64_t seed, int n_steps, int o
    number of launches and their total device time in ms since the last enable.  Ops are numbered
    as in the library's pass table (TWA_PROF_NOPS kinds); bytes_per_cell receives the pass's
    algorithmic DRAM traffic in bytes per cell of one launched field (pair or slot). */
-#define TWA_PROF_NOPS 12
+#define TWA_PROF_NOPS 14
 int twa_profile_enable(twa_handle* h, int on);
 int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_ms, double* bytes_per_cell,
                      long long* fields_per_launch, long long* cells);

@@ -18,7 +18,7 @@ TWA_NSCALARS = 8
 SCALAR_NAMES = ("Q", "corr", "mass", "mass_cl", "nonfinite", "nk_sum", "drho_l2", "rhocl_l2")
 # Pass kinds of the FP32 pipelines, in the library's numbering (profiler ops).
 PASS_NAMES = ("drift", "kick_drift", "kick_drift_vinv", "drift_rho", "rho_fwd", "fwd", "fwd_mul_inv", "inv",
-              "kick_vinv", "kick_fwd_out", "steps_1d", "mul_inv")
+              "kick_vinv", "kick_fwd_out", "steps_1d", "mul_inv", "plane_kick_drift", "plane_poisson")
 TWA_PROF_NOPS = len(PASS_NAMES)
 
 

@@ -29,11 +29,14 @@
 
 using namespace twa;
 
-static_assert(OP_COUNT == TWA_PROF_NOPS, "profiler op table out of sync with the pass kinds");
+static_assert(OP_COUNT + PL_COUNT == TWA_PROF_NOPS, "profiler op table out of sync with the pass kinds");
 
 namespace {
 
-constexpr int MODE_1D = 0, MODE_2D = 1, MODE_3D = 2;
+constexpr int MODE_1D = 0, MODE_2D = 1, MODE_3D = 2, MODE_3DP = 3;
+// Profiler ids of the xy-plane passes follow the line-pass ops.
+constexpr int PROF_PLANE0 = OP_COUNT;
+constexpr int PROF_NOPS = OP_COUNT + PL_COUNT;
 
 struct Inst {
     int dim = 1;
@@ -95,10 +98,10 @@ struct twa_handle {
     };
     std::vector<ProfRec> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
-    long long prof_launches[OP_COUNT] = {};
-    double prof_ms[OP_COUNT] = {};
-    long long prof_fields[OP_COUNT] = {};
-    long long prof_cells[OP_COUNT] = {};
+    long long prof_launches[OP_COUNT + PL_COUNT] = {};
+    double prof_ms[OP_COUNT + PL_COUNT] = {};
+    long long prof_fields[OP_COUNT + PL_COUNT] = {};
+    long long prof_cells[OP_COUNT + PL_COUNT] = {};
 };
 
 namespace {
@@ -300,6 +303,76 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
 }
 
 
+int dispatch_plane(int N, int pop, int lines, dim3 grid, const PassArgs& a, cudaStream_t st, bool prep) {
+    switch (N) {
+        case 16: return launch_plane<16>(pop, lines, grid, a, st, prep);
+        case 32: return launch_plane<32>(pop, lines, grid, a, st, prep);
+        case 64: return launch_plane<64>(pop, lines, grid, a, st, prep);
+        case 128: return launch_plane<128>(pop, lines, grid, a, st, prep);
+        case 256: return launch_plane<256>(pop, lines, grid, a, st, prep);
+        default: return -1;
+    }
+}
+
+bool plane_variant_ok(int N, int pop, int lines) {
+    switch (N) {
+        case 16: return has_plane_variant<16>(pop, lines);
+        case 32: return has_plane_variant<32>(pop, lines);
+        case 64: return has_plane_variant<64>(pop, lines);
+        case 128: return has_plane_variant<128>(pop, lines);
+        case 256: return has_plane_variant<256>(pop, lines);
+        default: return false;
+    }
+}
+
+// One xy-plane pass over all z-planes of every pair of instance I (3D, nx = ny).
+int run_plane(twa_handle* h, Inst& I, float2* psi, int pop, double kick_frac, cudaStream_t st, int force_lines = 0) {
+    const int N = I.n[0];
+    int lines = force_lines;
+    if (!lines) {
+        auto it = I.lines.find(key_of(3, pop));
+        lines = (it != I.lines.end()) ? it->second : std::min(N, std::max(1, 256 / plan_threads_per_line(N)));
+    }
+    if (!plane_variant_ok(N, pop, lines))
+        return fail(h, TWA_EINVAL, "no plane variant for N=" + std::to_string(N) + " lines=" + std::to_string(lines));
+    PassArgs a{};
+    a.psi = psi;
+    a.buf = I.vc;
+    a.tw = h->tw32[N];
+    a.ph = I.ph[0];
+    a.ph_lo = I.ph_lo[0];
+    a.ph2 = I.ph[1];
+    a.ph2_lo = I.ph_lo[1];
+    a.k2x = I.k2[0];
+    a.k2y = I.k2[1];
+    a.k2z = I.k2[2];
+    split_kick(h, I, kick_frac, a.kick, a.kick_lo);
+    a.cells = I.cells;
+    a.n_slots = I.n_slots;
+    a.n_pairs = I.n_pairs;
+    a.lx = I.lg[0];
+    a.lxy = I.lg[0] + I.lg[1];
+    a.post = 1.0f;
+    const dim3 grid((unsigned)I.n[2], (unsigned)I.n_pairs, 1);
+    const long long pk = (1LL << 40) | ((long long)N << 24) | ((long long)pop << 16) | lines;
+    if (!h->prepared.count(pk)) {
+        if (dispatch_plane(N, pop, lines, grid, a, st, true) != 0) return fail(h, TWA_ECUDA, "cudaFuncSetAttribute failed");
+        h->prepared.insert(pk);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->prof_on) {
+        RC(prof_events(h, &e0, &e1));
+        CU(cudaEventRecord(e0, st));
+    }
+    if (dispatch_plane(N, pop, lines, grid, a, st, false) != 0) return fail(h, TWA_EINVAL, "plane dispatch failed");
+    if (h->prof_on) {
+        CU(cudaEventRecord(e1, st));
+        h->prof_pending.push_back({PROF_PLANE0 + pop, e0, e1, (long long)I.n_pairs, I.cells});
+    }
+    ++h->launches;
+    return 0;
+}
+
 float2* inst_psi(Inst& I, void* psi) { return static_cast<float2*>(psi) + I.off; }
 
 // V of every field from its density (a synchronized batch, nothing pending).
@@ -314,6 +387,11 @@ int poisson_init(twa_handle* h, Inst& I, float2* psi, cudaStream_t st) {
             RC(run_pass(h, I, psi, 1, OP_RHO_FWD, 0.0, I.vc, nullptr, P, st));
             RC(run_pass(h, I, psi, 0, OP_FWD_MUL_INV, 0.0, I.vc, nullptr, P, st));
             RC(run_pass(h, I, psi, 1, OP_INV, 0.0, I.vc, nullptr, P, st));
+            break;
+        case MODE_3DP:
+            RC(run_pass(h, I, psi, 2, OP_RHO_FWD, 0.0, I.vc, nullptr, P, st));
+            RC(run_plane(h, I, psi, PL_POISSON, 0.0, st));
+            RC(run_pass(h, I, psi, 2, OP_INV, 0.0, I.vc, nullptr, P, st));
             break;
         default:
             RC(run_pass(h, I, psi, 2, OP_RHO_FWD, 0.0, I.vc, nullptr, P, st));
@@ -331,7 +409,12 @@ int steps_f32(twa_handle* h, Inst& I, float2* psi, int n, double a_first, cudaSt
     if (I.mode == MODE_1D) return run_pass(h, I, psi, 0, OP_STEPS_1D, a_first, I.vc, nullptr, P, st, n);
     for (int s = 0; s < n; ++s) {
         const double k = (s == 0) ? a_first : 1.0;
-        if (I.mode == MODE_2D) {
+        if (I.mode == MODE_3DP) {
+            RC(run_plane(h, I, psi, PL_KICK_DRIFT, k, st));
+            RC(run_pass(h, I, psi, 2, OP_DRIFT_RHO, 0.0, I.vc, nullptr, P, st));
+            RC(run_plane(h, I, psi, PL_POISSON, 0.0, st));
+            RC(run_pass(h, I, psi, 2, OP_INV, 0.0, I.vc, nullptr, P, st));
+        } else if (I.mode == MODE_2D) {
             RC(run_pass(h, I, psi, 0, OP_KICK_DRIFT, k, I.vc, nullptr, P, st));
             RC(run_pass(h, I, psi, 1, OP_DRIFT_RHO, 0.0, I.vc, nullptr, P, st));
             RC(run_pass(h, I, psi, 0, OP_FWD_MUL_INV, 0.0, I.vc, nullptr, P, st));
@@ -567,6 +650,7 @@ int twa_create(twa_handle** out, const twa_grid* grids, const twa_params* p, int
         I.off = off;
         off += (size_t)I.n_slots * I.cells;
         I.mode = (g.dim == 1) ? MODE_1D : (g.dim == 2 ? MODE_2D : MODE_3D);
+        if (g.dim == 3 && I.n[0] == I.n[1] && I.n[0] >= 16 && I.n[0] <= 256) I.mode = MODE_3DP;
         h->in.push_back(I);
     }
     int rc = 0;
@@ -838,7 +922,7 @@ int twa_profile_enable(twa_handle* h, int on) {
         h->prof_pool.push_back(r.b);
     }
     h->prof_pending.clear();
-    for (int i = 0; i < OP_COUNT; ++i) {
+    for (int i = 0; i < PROF_NOPS; ++i) {
         h->prof_launches[i] = 0;
         h->prof_ms[i] = 0.0;
     }
@@ -849,7 +933,7 @@ int twa_profile_enable(twa_handle* h, int on) {
 int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_ms, double* bytes_per_cell,
                      long long* fields_per_launch, long long* cells) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
-    if (op < 0 || op >= OP_COUNT) return fail(h, TWA_EINVAL, "twa_profile_read: bad op");
+    if (op < 0 || op >= PROF_NOPS) return fail(h, TWA_EINVAL, "twa_profile_read: bad op");
     for (auto& r : h->prof_pending) {
         CU(cudaEventSynchronize(r.b));
         float ms = 0.f;
@@ -864,7 +948,7 @@ int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_m
     h->prof_pending.clear();
     // Algorithmic DRAM bytes per cell of one launched field (a pair of slots or one slot):
     // every complex value read or written once (8 bytes), the Poisson field once per pair.
-    static const double bpc[OP_COUNT] = {
+    static const double bpc[OP_COUNT + PL_COUNT] = {
         16.0,  // OP_DRIFT: psi read + write
         40.0,  // OP_KICK_DRIFT: W read, 2 x (psi read + write)
         40.0,  // OP_KICK_DRIFT_VINV
@@ -877,6 +961,8 @@ int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_m
         40.0,  // OP_KICK_FWD_OUT: W read, 2 x (psi read + spectrum write)
         48.0,  // OP_STEPS_1D: per pair and step if the fields streamed (they stay on chip)
         16.0,  // OP_MUL_INV
+        40.0,  // PL_KICK_DRIFT: W read once from DRAM, 2 x (psi read + write); row/column re-reads hit L2
+        16.0,  // PL_POISSON: W read + write
     };
     if (launches) *launches = h->prof_launches[op];
     if (total_ms) *total_ms = h->prof_ms[op];
@@ -933,6 +1019,67 @@ void write_cache(const char* path, const std::map<std::string, int>& m) {
 
 }  // namespace
 
+namespace {
+
+struct TunePass {
+    int axis, op, fields;  // axis 3 = xy-plane pass (op = plane op)
+    float2* buf;
+    float2* out;
+};
+
+int time_variant(twa_handle* h, Inst& I, float2* f, const TunePass& ps, int l, cudaStream_t st, cudaEvent_t e0,
+                 cudaEvent_t e1, float* ms) {
+    const int ns = (ps.op == OP_STEPS_1D && ps.axis == 0) ? 4 : 0;
+    auto once = [&]() -> int {
+        if (ps.axis == 3) return run_plane(h, I, f, ps.op, 0.0, st, l);
+        return run_pass(h, I, f, ps.axis, ps.op, 0.0, ps.buf, ps.out, ps.fields, st, ns, l);
+    };
+    RC(once());
+    CU(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) RC(once());
+    CU(cudaEventRecord(e1, st));
+    CU(cudaEventSynchronize(e1));
+    CU(cudaEventElapsedTime(ms, e0, e1));
+    return 0;
+}
+
+int tune_passes(twa_handle* h, Inst& I, float2* f, const std::vector<TunePass>& passes, std::map<std::string, int>& cache,
+                cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+    const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512};
+    for (const auto& ps : passes) {
+        const int N = I.n[ps.axis == 3 ? 0 : ps.axis];
+        auto ok = [&](int l) {
+            if (ps.axis == 3) return plane_variant_ok(N, ps.op, l);
+            if (!variant_ok(N, ps.op, ps.axis > 0, l)) return false;
+            return !(ps.op != OP_STEPS_1D && ps.axis == 0 && l > I.cells / I.n[0]);
+        };
+        const std::string key = tune_key(I, ps.axis, ps.op);
+        auto hit = cache.find(key);
+        if (hit != cache.end() && ok(hit->second)) {
+            I.lines[key_of(ps.axis, ps.op)] = hit->second;
+            continue;
+        }
+        float best = 1e30f;
+        int best_l = 0;
+        for (int l : cand) {
+            if (!ok(l)) continue;
+            float ms = 0.f;
+            RC(time_variant(h, I, f, ps, l, st, e0, e1, &ms));
+            if (ms < best) {
+                best = ms;
+                best_l = l;
+            }
+        }
+        if (best_l) {
+            I.lines[key_of(ps.axis, ps.op)] = best_l;
+            cache[key] = best_l;
+        }
+    }
+    return 0;
+}
+
+}  // namespace
+
 extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, void* stream) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     if (!psi) return fail(h, TWA_EINVAL, "twa_autotune: null buffer");
@@ -942,62 +1089,56 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512};
     for (auto& I : h->in) {
         float2* f = inst_psi(I, psi);
-        struct P {
-            int axis, op, fields;
-            float2* buf;
-            float2* out;
-        };
-        std::vector<P> passes;
         const int Pn = I.n_pairs, Sn = I.n_slots;
+        std::vector<TunePass> passes;
         if (I.mode == MODE_1D) {
             passes = {{0, OP_STEPS_1D, Pn, I.vc, nullptr}};
         } else if (I.mode == MODE_2D) {
             passes = {{0, OP_KICK_DRIFT, Pn, I.vc, nullptr}, {1, OP_DRIFT_RHO, Pn, I.vc, nullptr},
                       {0, OP_FWD_MUL_INV, Pn, I.vc, nullptr}, {1, OP_INV, Pn, I.vc, nullptr},
                       {1, OP_RHO_FWD, Pn, I.vc, nullptr}};
-            if (I.spec) passes.push_back({1, OP_FWD, Sn, I.spec, nullptr});
         } else {
+            // both 3D pipelines: the axis passes and, for square xy planes, the fused plane passes
             passes = {{0, OP_KICK_DRIFT_VINV, Pn, I.vc, nullptr}, {1, OP_DRIFT, Sn, I.vc, nullptr},
                       {2, OP_DRIFT_RHO, Pn, I.vc, nullptr}, {0, OP_FWD, Pn, I.vc, nullptr},
                       {1, OP_FWD_MUL_INV, Pn, I.vc, nullptr}, {2, OP_INV, Pn, I.vc, nullptr},
                       {2, OP_RHO_FWD, Pn, I.vc, nullptr}, {0, OP_INV, Pn, I.vc, nullptr},
                       {0, OP_KICK_VINV, Pn, I.vc, nullptr}};
-            if (I.spec) {
-                passes.push_back({1, OP_FWD, Sn, I.spec, nullptr});
-                passes.push_back({2, OP_FWD, Sn, I.spec, nullptr});
+            if (I.mode == MODE_3DP) {
+                passes.push_back({3, PL_KICK_DRIFT, Pn, I.vc, nullptr});
+                passes.push_back({3, PL_POISSON, Pn, I.vc, nullptr});
             }
         }
-        for (const auto& ps : passes) {
-            const std::string key = tune_key(I, ps.axis, ps.op);
+        if (I.spec) {
+            passes.push_back({0, OP_KICK_FWD_OUT, Pn, I.vc, I.spec});
+            for (int ax = 1; ax < I.dim; ++ax) passes.push_back({ax, OP_FWD, Sn, I.spec, nullptr});
+        }
+        RC(tune_passes(h, I, f, passes, cache, st, e0, e1));
+        if (I.mode == MODE_3DP || I.mode == MODE_3D) {
+            // pick the faster 3D pipeline by timing two whole steps of each
+            const std::string key = tune_key(I, 9, 0);
             auto hit = cache.find(key);
-            if (hit != cache.end() && variant_ok(I.n[ps.axis], ps.op, ps.axis > 0, hit->second)) {
-                I.lines[key_of(ps.axis, ps.op)] = hit->second;
-                continue;
-            }
-            float best = 1e30f;
-            int best_l = 0;
-            for (int l : cand) {
-                if (!variant_ok(I.n[ps.axis], ps.op, ps.axis > 0, l)) continue;
-                if (ps.op != OP_STEPS_1D && ps.axis == 0 && l > I.cells / I.n[0]) continue;
-                const int ns = (ps.op == OP_STEPS_1D) ? 4 : 0;
-                RC(run_pass(h, I, f, ps.axis, ps.op, 0.0, ps.buf, ps.out, ps.fields, st, ns, l));
-                CU(cudaEventRecord(e0, st));
-                for (int r = 0; r < 3; ++r) RC(run_pass(h, I, f, ps.axis, ps.op, 0.0, ps.buf, ps.out, ps.fields, st, ns, l));
-                CU(cudaEventRecord(e1, st));
-                CU(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CU(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) {
-                    best = ms;
-                    best_l = l;
+            const bool eligible = I.n[0] == I.n[1] && I.n[0] >= 16 && I.n[0] <= 256;
+            if (!eligible) {
+                I.mode = MODE_3D;
+            } else if (hit != cache.end()) {
+                I.mode = hit->second ? MODE_3DP : MODE_3D;
+            } else {
+                float t[2] = {0.f, 0.f};
+                const int modes[2] = {MODE_3D, MODE_3DP};
+                for (int m = 0; m < 2; ++m) {
+                    I.mode = modes[m];
+                    RC(steps_f32(h, I, f, 1, 1.0, st));
+                    CU(cudaEventRecord(e0, st));
+                    RC(steps_f32(h, I, f, 2, 1.0, st));
+                    CU(cudaEventRecord(e1, st));
+                    CU(cudaEventSynchronize(e1));
+                    CU(cudaEventElapsedTime(&t[m], e0, e1));
                 }
-            }
-            if (best_l) {
-                I.lines[key_of(ps.axis, ps.op)] = best_l;
-                cache[key] = best_l;
+                I.mode = (t[1] <= t[0]) ? MODE_3DP : MODE_3D;
+                cache[key] = (I.mode == MODE_3DP) ? 1 : 0;
             }
         }
         CU(cudaMemsetAsync(I.vc, 0, (size_t)I.n_pairs * I.cells * sizeof(float2), st));

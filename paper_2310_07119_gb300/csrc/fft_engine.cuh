@@ -129,7 +129,13 @@ TWA_PLAN(2048, 16, 3, 16, 16, 8)
 #undef TWA_PLAN
 
 __host__ __device__ constexpr int pad_idx(int i) { return i + (i >> 4); }
+// Shared-memory line stride.  Column passes (lanes = lines): odd, so 16 lanes of a 64-bit access
+// phase fall in distinct banks.  Row passes (lanes = positions, T < 16 threads per line): the lines
+// sharing an access phase start 2 T banks apart, so each uses its own window of banks.
 __host__ __device__ constexpr int line_stride(int n) { return (pad_idx(n) & 1) ? pad_idx(n) : pad_idx(n) + 1; }
+__host__ __device__ constexpr int line_stride_rows(int n, int t) {
+    return (t >= 16) ? pad_idx(n) : pad_idx(n) + ((t - pad_idx(n) % 16) % 16 + 16) % 16;
+}
 
 template <int N, bool INV, int s>
 struct StageInfo {

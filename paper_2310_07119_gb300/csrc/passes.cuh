@@ -56,6 +56,8 @@ struct PassArgs {
     int lx, lxy;            // log2 nx, log2 (nx ny)
     int nsteps;             // OP_STEPS_1D
     float post;             // OP_FWD: factor applied before the store (1, or 1/N to undo an inverse)
+    const float2* ph2;      // plane passes: kinetic phase along y (hi, lo)
+    const float2* ph2_lo;
 };
 
 // z * exp(-i theta), theta reduced to [-pi, pi] by a two-constant (Cody-Waite) split of 2 pi.
@@ -73,11 +75,21 @@ __device__ __forceinline__ float2 kick_w(float2 z, float k_hi, float k_lo, float
     return kick_phase(z, fmaf(k_hi, W, k_lo * W));
 }
 
+// At least 512 resident threads (16 warps) per SM so that one CTA's loads overlap another's
+// transforms; this caps the registers per thread at 128.
+constexpr int min_ctas(int threads) { return threads >= 512 ? 1 : 512 / threads; }
+
+// Ops that keep a per-thread array across the two streams of a pair park it in a thread-private
+// shared-memory stash (RMAX float2 per thread, after the exchange lines) instead of registers.
+constexpr bool op_stash(int op) {
+    return op == OP_DRIFT_RHO || op == OP_RHO_FWD || op == OP_KICK_DRIFT_VINV || op == OP_KICK_VINV;
+}
+
 template <int N, int LINES, bool STRIDED, int OP>
-__global__ void __launch_bounds__(LINES * Plan<N>::T)
+__global__ void __launch_bounds__(LINES * Plan<N>::T, (OP == OP_STEPS_1D) ? 1 : min_ctas(LINES * Plan<N>::T))
 k_line(const PassArgs a) {
     using P = Plan<N>;
-    constexpr int T = P::T, RMAX = P::RMAX, LS = line_stride(N);
+    constexpr int T = P::T, RMAX = P::RMAX, LS = STRIDED ? line_stride(N) : line_stride_rows(N, T);
     constexpr bool WARP = !STRIDED && (T <= 32);
     constexpr unsigned MASK = (LINES * T >= 32) ? 0xffffffffu : ((1u << (LINES * T)) - 1u);
     extern __shared__ float2 smem[];
@@ -86,23 +98,26 @@ k_line(const PassArgs a) {
     const int t = STRIDED ? (tid / LINES) : (tid % T);
     float2* sm = smem + l * LS;
     const float4* __restrict__ tw = a.tw;
+    constexpr int NTH = LINES * T;
+    float2* stash = smem + LINES * LS + tid;     // stash[i * NTH]: slot i of this thread
 
-    // Line of this thread; lines past the end of the field (partial tiles of small grids) run on a
+    // Line of this thread (element offset of its first cell inside a field; a field has fewer
+    // than 2^31 cells); lines past the end of the field (partial tiles of small grids) run on a
     // clamped valid line and store nothing, so every thread reaches every barrier.
-    long long base;
+    int base;
     bool act;
     if constexpr (STRIDED) {
         const int tq = (a.Qn + LINES - 1) / LINES;
         const int q = (int)(blockIdx.x % tq) * LINES + l;
         act = q < a.Qn;
-        base = (long long)(act ? q : a.Qn - 1) + (long long)(blockIdx.x / tq) * a.OS;
+        base = (act ? q : a.Qn - 1) + (int)(blockIdx.x / tq) * (int)a.OS;
     } else {
-        const long long rows = a.cells / N;
-        const long long row = (long long)blockIdx.x * LINES + l;
+        const int rows = (int)(a.cells / N);
+        const int row = (int)blockIdx.x * LINES + l;
         act = row < rows;
         base = (act ? row : rows - 1) * N;
     }
-    const long long S = STRIDED ? a.S : 1;
+    const int S = STRIDED ? a.S : 1;
     const int f = blockIdx.y;
     float2 v[RMAX];
 
@@ -136,7 +151,7 @@ k_line(const PassArgs a) {
         const int mx = (1 << a.lx) - 1, my = (1 << (a.lxy - a.lx)) - 1;
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
-            const long long e = base + pos_spec<N>(t, i) * S;
+            const int e = base + pos_spec<N>(t, i) * S;
             const float k2 = __ldg(&a.k2x[e & mx]) + __ldg(&a.k2y[(e >> a.lx) & my]) + __ldg(&a.k2z[e >> a.lxy]);
             const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
             w[i] = make_float2(w[i].x * m, w[i].y * m);
@@ -163,7 +178,7 @@ k_line(const PassArgs a) {
             if (a.kick != 0.f) {
 #pragma unroll
                 for (int i = 0; i < RMAX; ++i) {
-                    const long long e = base + pos_nat<N>(t, i) * S;
+                    const int e = base + pos_nat<N>(t, i) * S;
                     const float2 c = VC[e];
                     v[i] = kick_w(F[e], a.kick, a.kick_lo, h ? c.y : c.x);
                 }
@@ -179,9 +194,11 @@ k_line(const PassArgs a) {
             }
         }
     } else if constexpr (OP == OP_KICK_DRIFT_VINV || OP == OP_KICK_VINV) {
-        float2 w[RMAX];
-        load_spec(w, a.buf + (long long)f * a.cells);
-        fft_line<N, true, WARP, MASK>(w, t, sm, tw);
+        // inverse transform of the pair's Poisson line, parked in the stash for both streams
+        load_spec(v, a.buf + (long long)f * a.cells);
+        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) stash[i * NTH] = v[i];
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
             const int slot = 2 * f + h;
@@ -189,12 +206,16 @@ k_line(const PassArgs a) {
             float2* F = a.psi + (long long)slot * a.cells;
             load_nat(v, F);
 #pragma unroll
-            for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, h ? w[i].y : w[i].x);
+            for (int i = 0; i < RMAX; ++i) {
+                const float2 w = stash[i * NTH];
+                v[i] = kick_w(v[i], a.kick, a.kick_lo, h ? w.y : w.x);
+            }
             if constexpr (OP == OP_KICK_DRIFT_VINV) drift(v);
             store_nat(v, F);
         }
     } else if constexpr (OP == OP_DRIFT_RHO || OP == OP_RHO_FWD) {
-        float2 c[RMAX];
+        // density of slot 2f parked in the stash while slot 2f+1 is processed, then packed as
+        // rho_0 + i rho_1 in v and transformed (one loop body: no hoisting of the second stream)
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
             const int slot = 2 * f + h;
@@ -209,14 +230,16 @@ k_line(const PassArgs a) {
 #pragma unroll
                 for (int i = 0; i < RMAX; ++i) v[i] = make_float2(0.f, 0.f);
             }
+            if (h == 0) {
 #pragma unroll
-            for (int i = 0; i < RMAX; ++i) {
-                const float r2 = fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
-                if (h == 0) c[i].x = r2; else c[i].y = r2;
+                for (int i = 0; i < RMAX; ++i) stash[i * NTH].x = fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
+            } else {
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) v[i] = make_float2(stash[i * NTH].x, fmaf(v[i].x, v[i].x, v[i].y * v[i].y));
             }
         }
-        fft_line<N, false, WARP, MASK>(c, t, sm, tw);
-        store_spec(c, a.buf + (long long)f * a.cells);
+        fft_line<N, false, WARP, MASK>(v, t, sm, tw);
+        store_spec(v, a.buf + (long long)f * a.cells);
     } else if constexpr (OP == OP_FWD) {
         float2* F = a.buf + (long long)f * a.cells;
         load_nat(v, F);
@@ -295,6 +318,133 @@ k_line(const PassArgs a) {
         }
     }
 }
+
+// ---------------------------------------------------------------------------------------------
+// xy-plane passes of 3D fields (nx = ny = N): one CTA owns one z-plane of one pair of slots.  The
+// rows are transformed first and written back to the field; after a CTA barrier the columns are
+// read back with L2-only loads (the plane was just written, so it is L2-resident and DRAM sees one
+// read and one write of it) and transformed.  This fuses the x and y passes without holding a plane
+// in shared memory.
+//   PL_KICK_DRIFT : per slot of the pair: kick with the real Poisson field, drift_x (rows), drift_y
+//   PL_POISSON    : Poisson field plane at fixed k_z: FFT_x (rows), FFT_y, 1/k^2, iFFT_y (columns),
+//                   iFFT_x (rows)
+enum PlaneOp : int { PL_KICK_DRIFT = 0, PL_POISSON = 1, PL_COUNT };
+
+template <int N, int L, int POP>
+__global__ void __launch_bounds__(L * Plan<N>::T, min_ctas(L * Plan<N>::T))
+k_plane(const PassArgs a) {
+    using P = Plan<N>;
+    constexpr int T = P::T, RMAX = P::RMAX;
+    constexpr int LSR = line_stride_rows(N, T), LSC = line_stride(N);
+    constexpr bool WARP = (T <= 32);
+    constexpr unsigned MASK = (L * T >= 32) ? 0xffffffffu : ((1u << (L * T)) - 1u);
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x;
+    const int lr = tid / T, tr = tid % T;        // row mapping: lanes walk along a row
+    const int lc = tid % L, tc = tid / L;        // column mapping: lanes walk across columns
+    const float4* __restrict__ tw = a.tw;
+    const int plane = (int)blockIdx.x * N * N;
+    const int f = blockIdx.y;
+    float2 v[RMAX];
+
+    auto phase = [&](float2 (&w)[RMAX], const float2* ph, const float2* phl, int t) {
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+            const int k = pos_spec<N>(t, i);
+            w[i] = cmul_c(w[i], __ldg(&ph[k]), __ldg(&phl[k]));
+        }
+    };
+    auto poisson = [&](float2 (&w)[RMAX], int col) {
+        const int mx = (1 << a.lx) - 1, my = (1 << (a.lxy - a.lx)) - 1;
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+            const int e = plane + col + pos_spec<N>(tc, i) * N;
+            const float k2 = __ldg(&a.k2x[e & mx]) + __ldg(&a.k2y[(e >> a.lx) & my]) + __ldg(&a.k2z[e >> a.lxy]);
+            const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
+            w[i] = make_float2(w[i].x * m, w[i].y * m);
+        }
+    };
+
+    if constexpr (POP == PL_KICK_DRIFT) {
+        const float2* Wp = a.buf + (long long)f * a.cells + plane;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int slot = 2 * f + h;
+            if (slot >= a.n_slots) break;
+            float2* F = a.psi + (long long)slot * a.cells + plane;
+            float2* smr = smem + lr * LSR;
+#pragma unroll 1
+            for (int r0 = 0; r0 < N; r0 += L) {
+                const int row = (r0 + lr) * N;
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) {
+                    const int e = row + pos_nat<N>(tr, i);
+                    const float2 c = __ldcg(&Wp[e]);
+                    v[i] = kick_w(__ldcg(&F[e]), a.kick, a.kick_lo, h ? c.y : c.x);
+                }
+                fft_line<N, false, WARP, MASK>(v, tr, smr, tw);
+                phase(v, a.ph, a.ph_lo, tr);
+                fft_line<N, true, WARP, MASK>(v, tr, smr, tw);
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) F[row + pos_nat<N>(tr, i)] = v[i];
+            }
+            __syncthreads();
+            float2* smc = smem + lc * LSC;
+#pragma unroll 1
+            for (int c0 = 0; c0 < N; c0 += L) {
+                const int col = c0 + lc;
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) v[i] = __ldcg(&F[col + pos_nat<N>(tc, i) * N]);
+                fft_line<N, false, false>(v, tc, smc, tw);
+                phase(v, a.ph2, a.ph2_lo, tc);
+                fft_line<N, true, false>(v, tc, smc, tw);
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) F[col + pos_nat<N>(tc, i) * N] = v[i];
+            }
+            __syncthreads();
+        }
+    } else {
+        float2* Wp = a.buf + (long long)f * a.cells + plane;
+        float2* smr = smem + lr * LSR;
+        float2* smc = smem + lc * LSC;
+#pragma unroll 1
+        for (int r0 = 0; r0 < N; r0 += L) {
+            const int row = (r0 + lr) * N;
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) v[i] = __ldcg(&Wp[row + pos_nat<N>(tr, i)]);
+            fft_line<N, false, WARP, MASK>(v, tr, smr, tw);
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) Wp[row + pos_spec<N>(tr, i)] = v[i];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += L) {
+            const int col = c0 + lc;
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) v[i] = __ldcg(&Wp[col + pos_nat<N>(tc, i) * N]);
+            fft_line<N, false, false>(v, tc, smc, tw);
+            poisson(v, col);
+            fft_line<N, true, false>(v, tc, smc, tw);
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) Wp[col + pos_nat<N>(tc, i) * N] = v[i];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int r0 = 0; r0 < N; r0 += L) {
+            const int row = (r0 + lr) * N;
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) v[i] = __ldcg(&Wp[row + pos_spec<N>(tr, i)]);
+            fft_line<N, true, WARP, MASK>(v, tr, smr, tw);
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) Wp[row + pos_nat<N>(tr, i)] = v[i];
+        }
+    }
+}
+
+template <int N>
+int launch_plane(int pop, int lines, dim3 grid, const PassArgs& a, cudaStream_t st, bool prepare_only);
+template <int N>
+bool has_plane_variant(int pop, int lines);
 
 // Host-side launcher of one pass (defined per N in passes_n*.cu).
 struct LaunchCfg {

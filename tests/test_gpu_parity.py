@@ -39,6 +39,9 @@ def _cases():
         "3d_kgauss16": ti.small_workload("kgauss", 3, 16, 5, 100, n_tot=1e8, dt=DT_128),
         "3d_kgauss32_pi4": ti.small_workload("kgauss", 3, 32, 3, 100, n_tot=1e8),
         "3d_soliton32": ti.small_workload("soliton", 3, 32, 3, 100, n_tot=1e10, dt=DT_256),
+        # nx != ny: runs the per-axis 3D pipeline (square xy planes use the fused plane passes)
+        "3d_kgauss_32x16x16": ti.Workload("kgauss", ti.Grid(3, (32, 16, 16), 1.0),
+                                          ti.Physics(ti.HBAR_3D, 4 * np.pi, DT_128, 1e8), 4, 100, 10, 5, 4321),
     }
 
 
@@ -112,7 +115,7 @@ def test_f64_plain_path_matches_oracle(name):
     assert abs(m["scalars"][0].item() - mo["Q"]) < 1e-9 * max(1.0, abs(mo["Q"]))
 
 
-@pytest.mark.parametrize("name", ["2d_merger64", "3d_kgauss16", "1d_bump256"])
+@pytest.mark.parametrize("name", ["2d_merger64", "3d_kgauss16", "1d_bump256", "3d_kgauss_32x16x16"])
 def test_f32_moments_match_oracle(name):
     w = CASES[name]
     n = 30
