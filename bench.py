@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["twa", "reference"], default="twa")
     ap.add_argument("--no-extras", action="store_true", help="skip cpu/f64/cufft/e2e side measurements")
+    ap.add_argument("--streams", type=int, default=STREAMS, help="streams per batch (smaller batches for ncu captures)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default pass shapes, axis pipeline)")
     return ap.parse_args()
 
 
@@ -121,9 +123,9 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-def _workload():
+def _workload(streams=STREAMS):
     import twa_inputs as ti
-    return ti.workload_3d_condensation(GRID_M, STREAMS, 2000)
+    return ti.workload_3d_condensation(GRID_M, streams, 2000)
 
 
 def _oracle_rate(w, n_fields=2, budget_s=12.0):
@@ -264,11 +266,13 @@ def run_twa(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2310_07119_gb300 import Ensemble, twa_advance, twa_last_launch_count, twa_profile_enable, twa_profile_read
 
-    w = _workload()
-    ens = Ensemble([w.grid], w.phys.hbar_m, w.phys.C, w.phys.dt, w.phys.n_tot, [STREAMS], want_modes=True,
+    w = _workload(args.streams)
+    ns = args.streams
+    ens = Ensemble([w.grid], w.phys.hbar_m, w.phys.C, w.phys.dt, w.phys.n_tot, [ns], want_modes=True,
                    device=f"cuda:{local}")
     cl = w.psi_cl()
-    ens.autotune(os.path.join(tempfile.gettempdir(), "twa_tune_cache.json"))
+    if not args.no_tune:
+        ens.autotune(os.path.join(tempfile.gettempdir(), "twa_tune_cache.json"))
     ens.sample([cl], w.noise_seed)
     series_w = ens.new_series(max(1, args.warmup) * OUT_EVERY, OUT_EVERY)
     twa_advance(ens.h, ens.psi, max(1, args.warmup) * OUT_EVERY, OUT_EVERY, series_w)
@@ -296,7 +300,7 @@ def run_twa(args):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    cell_updates = STREAMS * w.grid.cells * OUT_EVERY * args.steps * world
+    cell_updates = ns * w.grid.cells * OUT_EVERY * args.steps * world
     value = cell_updates / (ms * 1e-3)
     sc = series.cpu().numpy()
 
@@ -316,9 +320,9 @@ def run_twa(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"3D Gaussian-random-field condensation {GRID_M}^3 x {STREAMS} streams (+ classical field), "
+        "config": {"workload": f"3D Gaussian-random-field condensation {GRID_M}^3 x {ns} streams (+ classical field), "
                                f"FP32 KDK dt={w.phys.dt:.4e}, moments every {OUT_EVERY} steps",
-                   "grid": [GRID_M] * 3, "streams": STREAMS, "kdk_steps_per_step": OUT_EVERY,
+                   "grid": [GRID_M] * 3, "streams": ns, "kdk_steps_per_step": OUT_EVERY,
                    "batch_bytes": int(ens.psi.numel() * 8), "l2": "inputs larger than L2 (4.2 GB batch)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -332,7 +336,7 @@ def run_twa(args):
         "moments_last": {"Q": float(sc[-1, 0, 0]), "corr": float(sc[-1, 0, 1]), "mass": float(sc[-1, 0, 2])},
         "clocks": clk.summary(),
     }
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and not args.no_extras and ns == STREAMS:
         line["e2e"] = _e2e(ens, w)
         ens.close()
         torch.cuda.empty_cache()

@@ -77,26 +77,55 @@ __global__ void k_kick_pairs(float2* __restrict__ psi, const float2* __restrict_
 }
 
 // Position-space moments (Eq. E[op], Eq. Q) of one instance, one thread per cell, streams summed
-// in slot order in FP64.  The pending half kick (kick = dt / (2 hbar), or 0) is applied on the fly
-// to the mean field; |psi|^2 does not depend on it.
+// in slot order in FP64 (each |psi|^2 is formed in FP32, exact to its rounding, then accumulated
+// in FP64).  The pending half kick (kick != 0) is applied on the fly to the mean field; |psi|^2
+// does not depend on it.  Four pairs are loaded per iteration to keep loads in flight.
 __global__ void k_moments_real(const float2* __restrict__ psi, const float2* __restrict__ buf,
                                long long cells, int n_slots, float kick, float kick_lo, double inv_ns, double weyl,
                                double* rho_mean, double* psi_mean, double* rho_cl, double* part) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double v[NP_REAL] = {0, 0, 0, 0, 0, 0};
     if (g < cells) {
-        double m2 = 0.0, pr = 0.0, pi = 0.0, bad = 0.0;
-        for (int s = 1; s < n_slots; ++s) {
-            const float2 z = psi[(long long)s * cells + g];
+        double m2 = 0.0, pr = 0.0, pi = 0.0;
+        int bad = 0;
+        auto add = [&](float2 z, float2 zk) {
+            bad += (!isfinite(z.x) || !isfinite(z.y)) ? 1 : 0;
+            m2 += (double)fmaf(z.x, z.x, z.y * z.y);
+            pr += (double)zk.x;
+            pi += (double)zk.y;
+        };
+        // slot 1 pairs with slot 0 (pair 0); then pairs p = 1.. hold slots 2p, 2p+1
+        {
+            const float2 z = psi[cells + g];
             float2 zk = z;
-            if (kick != 0.f) {
-                const float2 c = buf[(long long)(s >> 1) * cells + g];
-                zk = kick_w(z, kick, kick_lo, (s & 1) ? c.y : c.x);
+            if (kick != 0.f) zk = kick_w(z, kick, kick_lo, buf[g].y);
+            if (n_slots > 1) add(z, zk);
+        }
+        const int np = (n_slots + 1) / 2;
+        int p = 1;
+        for (; p + 3 < np; p += 4) {
+            float2 z[8], c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                z[2 * u] = psi[(long long)(2 * (p + u)) * cells + g];
+                z[2 * u + 1] = (2 * (p + u) + 1 < n_slots) ? psi[(long long)(2 * (p + u) + 1) * cells + g] : make_float2(0.f, 0.f);
+                c[u] = (kick != 0.f) ? buf[(long long)(p + u) * cells + g] : make_float2(0.f, 0.f);
             }
-            if (!isfinite(z.x) || !isfinite(z.y)) bad += 1.0;
-            m2 += (double)z.x * z.x + (double)z.y * z.y;
-            pr += zk.x;
-            pi += zk.y;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                add(z[2 * u], kick != 0.f ? kick_w(z[2 * u], kick, kick_lo, c[u].x) : z[2 * u]);
+                if (2 * (p + u) + 1 < n_slots)
+                    add(z[2 * u + 1], kick != 0.f ? kick_w(z[2 * u + 1], kick, kick_lo, c[u].y) : z[2 * u + 1]);
+            }
+        }
+        for (; p < np; ++p) {
+            const float2 c = (kick != 0.f) ? buf[(long long)p * cells + g] : make_float2(0.f, 0.f);
+            const float2 z0 = psi[(long long)(2 * p) * cells + g];
+            add(z0, kick != 0.f ? kick_w(z0, kick, kick_lo, c.x) : z0);
+            if (2 * p + 1 < n_slots) {
+                const float2 z1 = psi[(long long)(2 * p + 1) * cells + g];
+                add(z1, kick != 0.f ? kick_w(z1, kick, kick_lo, c.y) : z1);
+            }
         }
         const float2 z0 = psi[g];
         const double cl = (double)z0.x * z0.x + (double)z0.y * z0.y;
@@ -110,29 +139,42 @@ __global__ void k_moments_real(const float2* __restrict__ psi, const float2* __r
             psi_mean[2 * g + 1] = pi;
         }
         if (rho_cl) rho_cl[g] = cl;
-        if (!isfinite(z0.x) || !isfinite(z0.y)) bad += 1.0;
+        if (!isfinite(z0.x) || !isfinite(z0.y)) bad += 1;
         v[0] = m2 - (pr * pr + pi * pi);
         v[1] = (rm - cl) * (rm - cl);
         v[2] = cl * cl;
         v[3] = m2;
         v[4] = cl;
-        v[5] = bad;
+        v[5] = (double)bad;
     }
     block_reduce_store<NP_REAL>(v, part);
 }
 
-// Per-mode moments: a_k = sqrt(n dV / M) FFT(psi_s)_k (spec holds FFT(psi_s) for every slot).
+// Per-mode moments: a_k = sqrt(n dV / M) FFT(psi_s)_k (spec holds FFT(psi_s) for every slot);
+// |FFT|^2 formed in FP32, scaled and accumulated in FP64, eight slots loaded per iteration.
 __global__ void k_moments_modes(const float2* __restrict__ spec, long long cells, int n_slots, double anorm2,
                                 double inv_ns, double* nk_mean, double* nk_var, double* part) {
     const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double v[NP_MODES] = {0, 0};
     if (k < cells) {
         double a2s = 0.0, a4s = 0.0;
-        for (int s = 1; s < n_slots; ++s) {
+        int s = 1;
+        for (; s + 7 < n_slots; s += 8) {
+            float2 z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) z[u] = spec[(long long)(s + u) * cells + k];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const double a2 = anorm2 * (double)fmaf(z[u].x, z[u].x, z[u].y * z[u].y);
+                a2s += a2;
+                a4s = fma(a2, a2, a4s);
+            }
+        }
+        for (; s < n_slots; ++s) {
             const float2 z = spec[(long long)s * cells + k];
-            const double a2 = anorm2 * ((double)z.x * z.x + (double)z.y * z.y);
+            const double a2 = anorm2 * (double)fmaf(z.x, z.x, z.y * z.y);
             a2s += a2;
-            a4s += a2 * a2;
+            a4s = fma(a2, a2, a4s);
         }
         const double m2 = a2s * inv_ns, m4 = a4s * inv_ns;
         const double nk = m2 - 0.5;

@@ -147,3 +147,14 @@ def test_kerr_ensemble_matches_closed_forms():
 
 def test_q_physical_scaling():
     assert twa.q_physical(1e-3, 1e8, 1e98) == pytest.approx(1e-93)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_early_growth_of_Q_is_quadratic(seed):
+    # Sec. V.A: Q - Q(0) grows as t^2 at early times (Eq. DefinitionKappa's prefactor is garbled,
+    # so only the exponent is pinned)
+    g = ti.Grid.cube(1, 64)
+    psi = ti.cosine_overdensity(g, 0.5)
+    t, series, _ = twa.run(psi, 0.05, 4 * np.pi, 2e-3, 1.0, 1, 1e8, 400, seed, 60, 6, with_modes=False)
+    q = np.array([s["Q"] for s in series])
+    assert 1.7 < twa.stable_growth_exponent(t, q) < 2.3
