@@ -87,6 +87,7 @@ typedef struct {
 } twa_params;
 
 /* Device FP64 outputs of one instance's moments (Eq. E[op]); any pointer may be NULL to skip it.
+   nk_cl[cells]    = |a_k|^2 of the classical field (slot 0), same normalization (needs want_modes)
    rho_mean[cells] = mean_s |psi_s|^2 - 1/(2 n dV)   (Weyl symbol of psi^dag psi)
    psi_mean[2*cells] = mean_s psi_s                    (interleaved re, im)
    rho_cl[cells]   = |psi_cl|^2
@@ -100,6 +101,7 @@ typedef struct {
     double* nk_mean;
     double* nk_var;
     double* scalars;
+    double* nk_cl;
 } twa_moments_out;
 
 typedef struct twa_handle twa_handle;
@@ -175,6 +177,49 @@ int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_m
 #define TWA_STATIC_SCRATCH_ELEMS (1 << 19)
 int twa_step_batch_1d_static(const twa_grid* grid, const twa_params* p, int n_real, void* psi,
                              int n_steps, void* stream);
+
+/* ---- Learned correction surrogate (no counterpart in the paper) --------------------------------
+   A Fourier neural operator on the grid of Fourier modes of a grid^3 field: features of a TWA run
+   (classical occupation, a few-stream correction estimate, ...) -> the ensemble correction spectrum
+   <n_k> - n_k^cl.  h_0 = P x + p; z_l = Re A^H (R_l . A h_l) + W_l h_l + b_l; h_{l+1} = gelu(z_l)
+   (l < layers-1); y = Q h_L + q, with A the unitary 3D DFT restricted to |m_a| < modes.  Weights are
+   kept as an FP32 master vector and a BF16 copy used by the kernels (FP32 accumulation).  Flat
+   parameter order: P (width x c_in), p, then per layer R ((2 modes)^3 x width x width, re/im), W_l
+   (width x width), b_l, then Q (c_out x width), q.  Tensors are device float [B][C][grid^3].
+   Requires 2 (2 modes)^3 <= grid^3. */
+typedef struct {
+    int grid;
+    int width;
+    int modes;
+    int layers;
+    int c_in;
+    int c_out;
+} twa_fno_config;
+typedef struct twa_fno twa_fno;
+int twa_fno_create(twa_fno** out, const twa_fno_config* cfg, uint64_t seed);
+int twa_fno_destroy(twa_fno* f);
+long long twa_fno_num_params(const twa_fno* f);
+/* copy a flat FP32 parameter vector (device) in (resets the AdamW state) or out (which = 0: parameters,
+   1: accumulated gradients) */
+int twa_fno_set_params(twa_fno* f, const float* src, void* stream);
+int twa_fno_get_params(twa_fno* f, float* dst, int which, void* stream);
+/* forward for a batch of B inputs x[B][c_in][grid^3] -> y[B][c_out][grid^3]; keeps the activations
+   (x must stay valid until the matching backward) */
+int twa_fno_forward(twa_fno* f, const float* x, int B, float* y, void* stream);
+/* backward of the last forward: accumulates parameter gradients; dx (optional) = dL/dx */
+int twa_fno_backward(twa_fno* f, const float* dy, int B, float* dx, void* stream);
+int twa_fno_zero_grad(twa_fno* f, void* stream);
+/* AdamW step on the accumulated gradients (bias-corrected moments, decoupled weight decay) */
+int twa_fno_adamw(twa_fno* f, float lr, float beta1, float beta2, float eps, float weight_decay, void* stream);
+/* mean squared error of y against t (n floats) into *loss (device float); dy (optional) = dL/dy */
+int twa_fno_mse(twa_fno* f, const float* y, const float* t, long long n, float* loss, float* dy, void* stream);
+const char* twa_fno_last_error(const twa_fno* f);
+/* Input features x[4][grid^3] of one snapshot from device FP64 per-mode occupations (FFT order),
+   with nu = n_tot / grid^3: x0 = log10(1 + n_cl) / 8, x1 = (n_est - n_cl) / (n_cl + nu) (the
+   few-stream correction estimate, relative), x2 = log10(n_tot) - 9, x3 = |m| / (grid/2); and, if t is
+   not NULL, the target t[grid^3] = (n_ref - n_cl) / (n_cl + nu) from a reference ensemble. */
+int twa_fno_features(const double* nk_cl, const double* nk_est, const double* nk_ref, double n_tot, int grid,
+                     float* x, float* t, void* stream);
 
 /* Block on `stream` and report device-side failures recorded since the last call
    (TWA_ENONFINITE) or TWA_OK.  Clears the device error word. */

@@ -33,7 +33,12 @@ class Params(ctypes.Structure):
 
 
 class MomentsOut(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_void_p) for n in ("rho_mean", "psi_mean", "rho_cl", "nk_mean", "nk_var", "scalars")]
+    _fields_ = [(n, ctypes.c_void_p) for n in ("rho_mean", "psi_mean", "rho_cl", "nk_mean", "nk_var", "scalars",
+                                               "nk_cl")]
+
+
+class FnoConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("grid", "width", "modes", "layers", "c_in", "c_out")]
 
 
 _P = ctypes.c_void_p
@@ -55,6 +60,19 @@ _SIGS = {
     "twa_last_error": (ctypes.c_char_p, [_P]),
     "twa_autotune": (ctypes.c_int, [_P, _P, ctypes.c_char_p, _P]),
     "twa_last_launch_count": (ctypes.c_longlong, [_P]),
+    "twa_fno_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(FnoConfig), ctypes.c_uint64]),
+    "twa_fno_destroy": (ctypes.c_int, [_P]),
+    "twa_fno_num_params": (ctypes.c_longlong, [_P]),
+    "twa_fno_set_params": (ctypes.c_int, [_P, _P, _P]),
+    "twa_fno_get_params": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "twa_fno_forward": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
+    "twa_fno_backward": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
+    "twa_fno_zero_grad": (ctypes.c_int, [_P, _P]),
+    "twa_fno_adamw": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, _P]),
+    "twa_fno_mse": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P, _P, _P]),
+    "twa_fno_last_error": (ctypes.c_char_p, [_P]),
+    "twa_fno_features": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
 }
 
 _lib = None

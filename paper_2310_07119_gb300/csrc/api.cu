@@ -458,7 +458,7 @@ int moments_f32(twa_handle* h, Inst& I, float2* psi, double pend, const twa_mome
         RC(run_pass(h, I, psi, 0, OP_KICK_FWD_OUT, pend, I.vc, I.spec, I.n_pairs, st, 0, I.mode == MODE_1D ? 1 : 0));
         for (int ax = 1; ax < I.dim; ++ax) RC(run_pass(h, I, psi, ax, OP_FWD, 0.0, I.spec, nullptr, I.n_slots, st));
         launch_moments_modes(I.spec, I.cells, I.n_slots, h->p.n_tot * I.dV / (double)I.cells, 1.0 / ns,
-                             o ? o->nk_mean : nullptr, o ? o->nk_var : nullptr, I.part_m, st);
+                             o ? o->nk_mean : nullptr, o ? o->nk_var : nullptr, o ? o->nk_cl : nullptr, I.part_m, st);
         ++h->launches;
         nbm = nb;
     }

@@ -19,7 +19,7 @@ int launch_moments_real(const float2* psi, const float2* buf, long long cells, i
                         float kick_lo, double inv_ns, double weyl, double* rho_mean, double* psi_mean, double* rho_cl,
                         double* part, cudaStream_t st);
 int launch_moments_modes(const float2* spec, long long cells, int n_slots, double anorm2, double inv_ns,
-                         double* nk_mean, double* nk_var, double* part, cudaStream_t st);
+                         double* nk_mean, double* nk_var, double* nk_cl, double* part, cudaStream_t st);
 int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, int nb_m, double dV,
                           double q_offset, double* scalars, int* err_word, cudaStream_t st);
 int launch_store_series(const double* cur, double* series, int* counter, int n, cudaStream_t st);

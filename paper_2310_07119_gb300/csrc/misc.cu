@@ -153,7 +153,7 @@ __global__ void k_moments_real(const float2* __restrict__ psi, const float2* __r
 // Per-mode moments: a_k = sqrt(n dV / M) FFT(psi_s)_k (spec holds FFT(psi_s) for every slot);
 // |FFT|^2 formed in FP32, scaled and accumulated in FP64, eight slots loaded per iteration.
 __global__ void k_moments_modes(const float2* __restrict__ spec, long long cells, int n_slots, double anorm2,
-                                double inv_ns, double* nk_mean, double* nk_var, double* part) {
+                                double inv_ns, double* nk_mean, double* nk_var, double* nk_cl, double* part) {
     const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double v[NP_MODES] = {0, 0};
     if (k < cells) {
@@ -180,6 +180,10 @@ __global__ void k_moments_modes(const float2* __restrict__ spec, long long cells
         const double nk = m2 - 0.5;
         if (nk_mean) nk_mean[k] = nk;
         if (nk_var) nk_var[k] = m4 - m2 - nk * nk;
+        if (nk_cl) {
+            const float2 z = spec[k];
+            nk_cl[k] = anorm2 * ((double)z.x * z.x + (double)z.y * z.y);
+        }
         v[0] = nk;
     }
     block_reduce_store<NP_MODES>(v, part);
@@ -261,9 +265,9 @@ int launch_moments_real(const float2* psi, const float2* buf, long long cells, i
     return 0;
 }
 int launch_moments_modes(const float2* spec, long long cells, int n_slots, double anorm2, double inv_ns,
-                         double* nk_mean, double* nk_var, double* part, cudaStream_t st) {
+                         double* nk_mean, double* nk_var, double* nk_cl, double* part, cudaStream_t st) {
     k_moments_modes<<<moments_blocks(cells), 256, 0, st>>>(spec, cells, n_slots, anorm2, inv_ns, nk_mean,
-                                                           nk_var, part);
+                                                           nk_var, nk_cl, part);
     return 0;
 }
 int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, int nb_m, double dV,

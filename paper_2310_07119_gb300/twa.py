@@ -100,7 +100,8 @@ def twa_step_batch(h, psi, n_steps: int, stream=None) -> None:
 
 
 def twa_moments(h, inst: int, psi, out: dict, stream=None) -> None:
-    mo = L.MomentsOut(*[_ptr(out.get(k)) for k in ("rho_mean", "psi_mean", "rho_cl", "nk_mean", "nk_var", "scalars")])
+    mo = L.MomentsOut(*[_ptr(out.get(k)) for k in ("rho_mean", "psi_mean", "rho_cl", "nk_mean", "nk_var", "scalars",
+                                                    "nk_cl")])
     _check(_lib().twa_moments(h, int(inst), _ptr(psi), ctypes.byref(mo), _stream(stream)), h)
 
 
@@ -220,6 +221,7 @@ class Ensemble:
         if modes:
             out["nk_mean"] = torch.empty(c, **f64)
             out["nk_var"] = torch.empty(c, **f64)
+            out["nk_cl"] = torch.empty(c, **f64)
         twa_moments(self.h, inst, self.psi, out, stream)
         return out
 
