@@ -25,6 +25,7 @@
 
 #include "kernels.h"
 #include "passes.cuh"
+#include "pipe.cuh"
 #include "twa.h"
 
 using namespace twa;
@@ -197,7 +198,32 @@ int dispatch(int N, const LaunchCfg& c, const PassArgs& a, cudaStream_t st, bool
     }
 }
 
+constexpr int PIPE_FLAG = 1 << 16;  // "lines" values with this bit select the pipelined pass
+
+int dispatch_pipe(int N, const LaunchCfg& c, const PassArgs& a, int tiles, int n_items, cudaStream_t st, bool prep) {
+    switch (N) {
+        case 32: return launch_pipe<32>(c, a, tiles, n_items, st, prep);
+        case 64: return launch_pipe<64>(c, a, tiles, n_items, st, prep);
+        case 128: return launch_pipe<128>(c, a, tiles, n_items, st, prep);
+        case 256: return launch_pipe<256>(c, a, tiles, n_items, st, prep);
+        case 512: return launch_pipe<512>(c, a, tiles, n_items, st, prep);
+        default: return -1;
+    }
+}
+
+bool pipe_variant_ok(int N, int op, bool strided, int lines) {
+    switch (N) {
+        case 32: return has_pipe_variant<32>(op, strided, lines);
+        case 64: return has_pipe_variant<64>(op, strided, lines);
+        case 128: return has_pipe_variant<128>(op, strided, lines);
+        case 256: return has_pipe_variant<256>(op, strided, lines);
+        case 512: return has_pipe_variant<512>(op, strided, lines);
+        default: return false;
+    }
+}
+
 bool variant_ok(int N, int op, bool strided, int lines) {
+    if (lines & PIPE_FLAG) return pipe_variant_ok(N, op, strided, lines & ~PIPE_FLAG);
     switch (N) {
         case 8: return has_variant<8>(op, strided, lines);
         case 16: return has_variant<16>(op, strided, lines);
@@ -241,9 +267,11 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
         auto it = I.lines.find(key_of(axis, op));
         lines = (it != I.lines.end()) ? it->second : default_lines(N, strided, op);
     }
+    const bool pipe = (lines & PIPE_FLAG) != 0;
     if (!variant_ok(N, op, strided, lines))
         return fail(h, TWA_EINVAL, "no pass variant for N=" + std::to_string(N) + " op=" + std::to_string(op) +
                                        " lines=" + std::to_string(lines));
+    lines &= ~PIPE_FLAG;
     PassArgs a{};
     a.psi = psi;
     a.buf = buf;
@@ -282,9 +310,19 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
         const long long rows = I.cells / N;
         c.grid = dim3((unsigned)((rows + lines - 1) / lines), (unsigned)fields, 1);
     }
-    const long long pk = ((long long)N << 24) | ((long long)op << 16) | ((long long)strided << 12) | lines;
+    int tiles = 0, n_items = 0;
+    if (pipe) {
+        const long long lines_per_field = strided ? (I.cells / N) : (I.cells / N);
+        tiles = (int)(lines_per_field / lines);
+        n_items = tiles * fields;
+        if (lines_per_field % lines != 0 || (strided && stride % lines != 0))
+            return fail(h, TWA_EINVAL, "pipelined pass needs full tiles");
+    }
+    const long long pk = ((long long)pipe << 41) | ((long long)N << 24) | ((long long)op << 16) |
+                         ((long long)strided << 12) | lines;
     if (!h->prepared.count(pk)) {
-        if (dispatch(N, c, a, st, true) != 0) return fail(h, TWA_ECUDA, "cudaFuncSetAttribute failed");
+        const int rc = pipe ? dispatch_pipe(N, c, a, tiles, n_items, st, true) : dispatch(N, c, a, st, true);
+        if (rc != 0) return fail(h, TWA_ECUDA, "cudaFuncSetAttribute failed");
         h->prepared.insert(pk);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -292,7 +330,8 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
         RC(prof_events(h, &e0, &e1));
         CU(cudaEventRecord(e0, st));
     }
-    if (dispatch(N, c, a, st, false) != 0) return fail(h, TWA_EINVAL, "pass dispatch failed");
+    if ((pipe ? dispatch_pipe(N, c, a, tiles, n_items, st, false) : dispatch(N, c, a, st, false)) != 0)
+        return fail(h, TWA_EINVAL, "pass dispatch failed");
     if (h->prof_on) {
         CU(cudaEventRecord(e1, st));
         const long long nf = (op == OP_STEPS_1D) ? (long long)I.n_pairs * nsteps : (long long)fields;
@@ -1045,13 +1084,20 @@ int time_variant(twa_handle* h, Inst& I, float2* f, const TunePass& ps, int l, c
 
 int tune_passes(twa_handle* h, Inst& I, float2* f, const std::vector<TunePass>& passes, std::map<std::string, int>& cache,
                 cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-    const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512};
+    const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512, PIPE_FLAG | 4, PIPE_FLAG | 8, PIPE_FLAG | 16,
+                        PIPE_FLAG | 32, PIPE_FLAG | 64};
     for (const auto& ps : passes) {
         const int N = I.n[ps.axis == 3 ? 0 : ps.axis];
         auto ok = [&](int l) {
-            if (ps.axis == 3) return plane_variant_ok(N, ps.op, l);
+            if (ps.axis == 3) return (l & PIPE_FLAG) == 0 && plane_variant_ok(N, ps.op, l);
             if (!variant_ok(N, ps.op, ps.axis > 0, l)) return false;
-            return !(ps.op != OP_STEPS_1D && ps.axis == 0 && l > I.cells / I.n[0]);
+            const int ll = l & ~PIPE_FLAG;
+            if (l & PIPE_FLAG) {
+                long long stride = 1;
+                for (int b = 0; b < ps.axis; ++b) stride *= I.n[b];
+                if ((I.cells / N) % ll != 0 || (ps.axis > 0 && stride % ll != 0)) return false;
+            }
+            return !(ps.op != OP_STEPS_1D && ps.axis == 0 && ll > I.cells / I.n[0]);
         };
         const std::string key = tune_key(I, ps.axis, ps.op);
         auto hit = cache.find(key);

@@ -60,13 +60,22 @@ struct PassArgs {
     const float2* ph2_lo;
 };
 
-// z * exp(-i theta), theta reduced to [-pi, pi] by a two-constant (Cody-Waite) split of 2 pi.
+// z * exp(-i theta).  For |theta| <= 1/4 (every kick of the measured workloads) sin and cos are
+// their Taylor polynomials through theta^7 and theta^8 (truncation below 1e-11, so the result is
+// correctly rounded to float up to the rounding of the evaluation); otherwise theta is reduced to
+// [-pi, pi] by a two-constant (Cody-Waite) split of 2 pi and sincosf is used.
 __device__ __forceinline__ float2 kick_phase(float2 z, float theta) {
-    const float n = rintf(theta * 0.15915494309189535f);
-    float r = fmaf(-n, 6.28125f, theta);
-    r = fmaf(-n, 0.0019353071795862327f, r);
     float s, c;
-    sincosf(r, &s, &c);
+    if (fabsf(theta) <= 0.25f) {
+        const float t2 = theta * theta;
+        s = theta * fmaf(t2, fmaf(t2, fmaf(t2, -1.9841269841e-4f, 8.3333333333e-3f), -1.6666666667e-1f), 1.0f);
+        c = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 2.4801587302e-5f, -1.3888888889e-3f), 4.1666666667e-2f), -0.5f), 1.0f);
+    } else {
+        const float n = rintf(theta * 0.15915494309189535f);
+        float r = fmaf(-n, 6.28125f, theta);
+        r = fmaf(-n, 0.0019353071795862327f, r);
+        sincosf(r, &s, &c);
+    }
     return make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
 }
 

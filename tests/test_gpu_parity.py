@@ -267,3 +267,58 @@ def test_bench_size_sampled_realizations():
     r_got, r_ref = np.abs(sub) ** 2, np.abs(ref) ** 2
     rho_err = np.sqrt(np.sum((r_got - r_ref) ** 2, axis=(1, 2, 3)) / np.sum(r_ref ** 2, axis=(1, 2, 3)))
     assert np.all(rho_err < RHO_TOL), rho_err
+
+
+
+PIPE = 1 << 16     # flag on a pass's "lines" value selecting its cp.async-pipelined variant
+PIPE_OPS = (0, 1, 2, 3, 5, 6, 7)     # drift, kick_drift, kick_drift_vinv, drift_rho, fwd, fwd_mul_inv, inv
+THREADS_PER_LINE = {32: 2, 64: 8, 128: 8, 256: 16, 512: 32}    # N / registers-per-thread of the line FFT
+
+
+def _force_pipelined(w, path, axis_pipeline):
+    """Autotune cache that selects the pipelined variant of every line pass that has one."""
+    import json
+    n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)          # fastest axis first
+    key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
+    cache = {f"{key}:axis9:op0": 0 if axis_pipeline else 1}
+    for ax in range(w.grid.dim):
+        T = THREADS_PER_LINE[n[ax]]
+        lines = max(4 if ax > 0 else 1, 128 // T)
+        for op in PIPE_OPS:
+            cache[f"{key}:axis{ax}:op{op}"] = PIPE | lines
+    json.dump(cache, open(path, "w"))
+
+
+# line passes each pipeline runs per step: (axis, op)
+RUN_PASSES = {"3d_axis": [(0, 2), (1, 0), (2, 3), (0, 5), (1, 6), (2, 7)], "3d_plane": [(2, 3), (2, 7)],
+              "2d": [(0, 1), (1, 3), (0, 6), (1, 7)]}
+
+
+@pytest.mark.parametrize("name,axis_pipeline", [("3d_kgauss64", True), ("3d_kgauss64", False), ("2d_merger64", True)])
+def test_pipelined_passes_match_oracle(name, axis_pipeline, tmp_path):
+    """The pipelined line passes, forced through the autotune cache, against the oracle (the cache
+    the tuner writes back shows that it kept the pipelined variant of every pass the step runs)."""
+    import json
+    if name == "3d_kgauss64":
+        w = ti.small_workload("kgauss", 3, 64, 3, 40, n_tot=1e8, dt=DT_128)
+        runs = RUN_PASSES["3d_axis" if axis_pipeline else "3d_plane"]
+    else:
+        w = ti.small_workload("merger2d", 2, 64, 5, 40, n_tot=1e9, dt=DT_2D)
+        runs = RUN_PASSES["2d"]
+    path = str(tmp_path / "force_pipe.json")
+    _force_pipelined(w, path, axis_pipeline)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    ens.autotune(path)
+    chosen = json.load(open(path))
+    n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)
+    key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
+    for ax, op in runs:
+        assert chosen[f"{key}:axis{ax}:op{op}"] & PIPE, (ax, op)
+    if w.grid.dim == 3:
+        assert chosen[f"{key}:axis9:op0"] == (0 if axis_pipeline else 1)
+    ens.sample([cl], w.noise_seed)
+    ens.step(w.n_steps)
+    got = ens.fields(0).cpu().numpy().astype(np.complex128)
+    ref = oracle_batch(w, cl, w.n_steps)
+    assert np.all(field_rel_l2(got, ref, w.grid.dim) < F32_FIELD_TOL)
