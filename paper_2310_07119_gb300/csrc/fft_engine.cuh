@@ -121,20 +121,29 @@ TWA_PLAN(8, 8, 1, 8)
 TWA_PLAN(16, 16, 1, 16)
 TWA_PLAN(32, 16, 2, 16, 2)
 TWA_PLAN(64, 8, 2, 8, 8)
+#ifdef TWA_PLAN128_R8
+TWA_PLAN(128, 8, 3, 8, 8, 2)
+#else
 TWA_PLAN(128, 16, 2, 16, 8)
+#endif
 TWA_PLAN(256, 16, 2, 16, 16)
 TWA_PLAN(512, 16, 3, 16, 8, 4)
 TWA_PLAN(1024, 16, 3, 16, 16, 4)
 TWA_PLAN(2048, 16, 3, 16, 16, 8)
 #undef TWA_PLAN
 
-__host__ __device__ constexpr int pad_idx(int i) { return i + (i >> 4); }
+// Shared-memory slot of element i of a line of length n: one padding slot per 16 elements, and for
+// n = 64 and 128 (T = 8 threads per line, four lines per warp in row passes) one per 8 plus one per
+// 64, which makes the exchanges of both stage orders (forward 16|8, inverse 8|16) conflict-free.
+__host__ __device__ constexpr int pad_n(int n, int i) {
+    return (n == 64 || n == 128) ? i + (i >> 3) + (i >> 6) : i + (i >> 4);
+}
 // Shared-memory line stride.  Column passes (lanes = lines): odd, so 16 lanes of a 64-bit access
 // phase fall in distinct banks.  Row passes (lanes = positions, T < 16 threads per line): the lines
 // sharing an access phase start 2 T banks apart, so each uses its own window of banks.
-__host__ __device__ constexpr int line_stride(int n) { return (pad_idx(n) & 1) ? pad_idx(n) : pad_idx(n) + 1; }
+__host__ __device__ constexpr int line_stride(int n) { return (pad_n(n, n) & 1) ? pad_n(n, n) : pad_n(n, n) + 1; }
 __host__ __device__ constexpr int line_stride_rows(int n, int t) {
-    return (t >= 16) ? pad_idx(n) : pad_idx(n) + ((t - pad_idx(n) % 16) % 16 + 16) % 16;
+    return (t >= 16) ? pad_n(n, n) : pad_n(n, n) + ((t - pad_n(n, n) % 16) % 16 + 16) % 16;
 }
 
 template <int N, bool INV, int s>
@@ -204,14 +213,14 @@ struct FftStage {
                 const int j = t + T * b;
                 const int base = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
-                for (int r = 0; r < R; ++r) sm[pad_idx(base + r * NS)] = v[b * R + r];
+                for (int r = 0; r < R; ++r) sm[pad_n(N, base + r * NS)] = v[b * R + r];
             }
             line_sync<WARP, MASK>();
 #pragma unroll
             for (int b = 0; b < B2; ++b) {
                 const int j = t + T * b;
 #pragma unroll
-                for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pad_idx(j + r * (N / R2))];
+                for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pad_n(N, j + r * (N / R2))];
             }
             line_sync<WARP, MASK>();
             FftStage<N, INV, s + 1, WARP, MASK>::run(v, t, sm, tw);

@@ -76,23 +76,48 @@ __global__ void k_kick_pairs(float2* __restrict__ psi, const float2* __restrict_
     }
 }
 
+// Running sum of floats carried as an unevaluated pair hi + lo ("double-float"): each addition's
+// rounding error is recovered exactly (Knuth's two-sum) and the pair is renormalized (Dekker's
+// fast two-sum), so the sum keeps about 48 significant bits.  The moment kernels accumulate in
+// this form because this part's FP64 rate is 1/64 of its FP32 rate: FP64 adds would make them
+// compute-bound at several times their memory time.  Results are finished in FP64.
+struct DF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a) {
+        const float s = hi + a;
+        const float bp = s - hi;
+        float e = (hi - (s - bp)) + (a - bp);  // hi + a = s + e exactly
+        e += lo;
+        hi = s + e;
+        lo = e - (hi - s);
+    }
+    // add a * a exactly (the product's rounding error recovered with an fma)
+    __device__ __forceinline__ void add_sq(float a) {
+        const float p = a * a;
+        const float q = fmaf(a, a, -p);
+        add(p);
+        lo += q;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Position-space moments (Eq. E[op], Eq. Q) of one instance, one thread per cell, streams summed
-// in slot order in FP64 (each |psi|^2 is formed in FP32, exact to its rounding, then accumulated
-// in FP64).  The pending half kick (kick != 0) is applied on the fly to the mean field; |psi|^2
-// does not depend on it.  Four pairs are loaded per iteration to keep loads in flight.
+// in slot order (each |psi|^2 is formed in FP32, exact to its rounding, and summed in double-float).
+// The pending half kick (kick != 0) is applied on the fly to the mean field; |psi|^2 does not
+// depend on it.  Four pairs are loaded per iteration to keep loads in flight.
 __global__ void k_moments_real(const float2* __restrict__ psi, const float2* __restrict__ buf,
                                long long cells, int n_slots, float kick, float kick_lo, double inv_ns, double weyl,
                                double* rho_mean, double* psi_mean, double* rho_cl, double* part) {
     const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double v[NP_REAL] = {0, 0, 0, 0, 0, 0};
     if (g < cells) {
-        double m2 = 0.0, pr = 0.0, pi = 0.0;
+        DF m2, pr, pi;
         int bad = 0;
         auto add = [&](float2 z, float2 zk) {
             bad += (!isfinite(z.x) || !isfinite(z.y)) ? 1 : 0;
-            m2 += (double)fmaf(z.x, z.x, z.y * z.y);
-            pr += (double)zk.x;
-            pi += (double)zk.y;
+            m2.add(fmaf(z.x, z.x, z.y * z.y));
+            pr.add(zk.x);
+            pi.add(zk.y);
         };
         // slot 1 pairs with slot 0 (pair 0); then pairs p = 1.. hold slots 2p, 2p+1
         {
@@ -129,21 +154,19 @@ __global__ void k_moments_real(const float2* __restrict__ psi, const float2* __r
         }
         const float2 z0 = psi[g];
         const double cl = (double)z0.x * z0.x + (double)z0.y * z0.y;
-        m2 *= inv_ns;
-        pr *= inv_ns;
-        pi *= inv_ns;
-        const double rm = m2 - weyl;
+        const double m2d = m2.value() * inv_ns, prd = pr.value() * inv_ns, pid = pi.value() * inv_ns;
+        const double rm = m2d - weyl;
         if (rho_mean) rho_mean[g] = rm;
         if (psi_mean) {
-            psi_mean[2 * g] = pr;
-            psi_mean[2 * g + 1] = pi;
+            psi_mean[2 * g] = prd;
+            psi_mean[2 * g + 1] = pid;
         }
         if (rho_cl) rho_cl[g] = cl;
         if (!isfinite(z0.x) || !isfinite(z0.y)) bad += 1;
-        v[0] = m2 - (pr * pr + pi * pi);
+        v[0] = m2d - (prd * prd + pid * pid);
         v[1] = (rm - cl) * (rm - cl);
         v[2] = cl * cl;
-        v[3] = m2;
+        v[3] = m2d;
         v[4] = cl;
         v[5] = (double)bad;
     }
@@ -151,13 +174,14 @@ __global__ void k_moments_real(const float2* __restrict__ psi, const float2* __r
 }
 
 // Per-mode moments: a_k = sqrt(n dV / M) FFT(psi_s)_k (spec holds FFT(psi_s) for every slot);
-// |FFT|^2 formed in FP32, scaled and accumulated in FP64, eight slots loaded per iteration.
+// |FFT|^2 formed in FP32; the sums of |FFT|^2 and of its exact square kept in double-float, scaled
+// in FP64; eight slots loaded per iteration.
 __global__ void k_moments_modes(const float2* __restrict__ spec, long long cells, int n_slots, double anorm2,
                                 double inv_ns, double* nk_mean, double* nk_var, double* nk_cl, double* part) {
     const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double v[NP_MODES] = {0, 0};
     if (k < cells) {
-        double a2s = 0.0, a4s = 0.0;
+        DF a2s, a4s;
         int s = 1;
         for (; s + 7 < n_slots; s += 8) {
             float2 z[8];
@@ -165,18 +189,18 @@ __global__ void k_moments_modes(const float2* __restrict__ spec, long long cells
             for (int u = 0; u < 8; ++u) z[u] = spec[(long long)(s + u) * cells + k];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const double a2 = anorm2 * (double)fmaf(z[u].x, z[u].x, z[u].y * z[u].y);
-                a2s += a2;
-                a4s = fma(a2, a2, a4s);
+                const float q = fmaf(z[u].x, z[u].x, z[u].y * z[u].y);
+                a2s.add(q);
+                a4s.add_sq(q);
             }
         }
         for (; s < n_slots; ++s) {
             const float2 z = spec[(long long)s * cells + k];
-            const double a2 = anorm2 * (double)fmaf(z.x, z.x, z.y * z.y);
-            a2s += a2;
-            a4s = fma(a2, a2, a4s);
+            const float q = fmaf(z.x, z.x, z.y * z.y);
+            a2s.add(q);
+            a4s.add_sq(q);
         }
-        const double m2 = a2s * inv_ns, m4 = a4s * inv_ns;
+        const double m2 = anorm2 * a2s.value() * inv_ns, m4 = anorm2 * anorm2 * a4s.value() * inv_ns;
         const double nk = m2 - 0.5;
         if (nk_mean) nk_mean[k] = nk;
         if (nk_var) nk_var[k] = m4 - m2 - nk * nk;
