@@ -16,8 +16,41 @@
 
 namespace twa {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Packed two-lane FP32 arithmetic (PTX .f32x2, sm_100 and later): one instruction applies the same
+// operation to both components of a float2.  The transforms are bound by instruction issue, and
+// the additions of a butterfly and most of its constant products pair up this way.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+// a * b + c lane by lane, each lane rounded once
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return f2_add(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return f2_sub(a, b); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -58,6 +91,21 @@ constexpr float kSin32[32] = {
 constexpr float kCos32Lo[32] = {0.000000000e+00f, 2.973947311e-08f, 2.830749035e-08f, 1.687026374e-08f, 1.210161715e-08f, -1.176952125e-08f, 6.223350946e-09f, -1.670471400e-09f, 0.000000000e+00f, 1.670471539e-09f, -6.223350835e-09f, 1.176952158e-08f, -1.210161704e-08f, -1.687026385e-08f, -2.830749035e-08f, -2.973947311e-08f, 0.000000000e+00f, -2.973947311e-08f, -2.830749046e-08f, -1.687026396e-08f, -1.210161726e-08f, 1.176952136e-08f, -6.223351445e-09f, 1.670471067e-09f, 0.000000000e+00f, -1.670471428e-09f, 6.223351112e-09f, -1.176952169e-08f, 1.210161693e-08f, 1.687026374e-08f, 2.830749013e-08f, 2.973947300e-08f};
 constexpr float kSin32Lo[32] = {0.000000000e+00f, -1.670471483e-09f, 6.223350890e-09f, -1.176952136e-08f, 1.210161704e-08f, 1.687026374e-08f, 2.830749035e-08f, 2.973947311e-08f, 0.000000000e+00f, 2.973947311e-08f, 2.830749035e-08f, 1.687026396e-08f, 1.210161715e-08f, -1.176952136e-08f, 6.223351001e-09f, -1.670471123e-09f, 0.000000000e+00f, 1.670471372e-09f, -6.223350779e-09f, 1.176952158e-08f, -1.210161704e-08f, -1.687026374e-08f, -2.830749013e-08f, -2.973947300e-08f, 0.000000000e+00f, -2.973947311e-08f, -2.830749024e-08f, -1.687026396e-08f, -1.210161726e-08f, 1.176952136e-08f, -6.223351501e-09f, 1.670471012e-09f};
 
+// a * (c + i s) for a compile-time constant carried as hi (c, s) + lo (cl, sl), in packed form:
+// a (c, c) + (a.y, a.x) (-s, s), with the lo part entering the innermost products as in cmul_c.
+__device__ __forceinline__ float2 cmul_k(float2 a, float c, float s, float cl, float sl) {
+    const float2 as = make_float2(a.y, a.x);
+    const float2 l = f2_fma(as, make_float2(-sl, sl), f2_mul(a, make_float2(cl, cl)));
+    return f2_fma(a, make_float2(c, c), f2_fma(as, make_float2(-s, s), l));
+}
+// a * (sx + i sy) c for signs sx, sy = +-1 and c = cos(pi / 4) carried as ch + cl: the rotation is
+// u = a + (sy / sx) i a (exact up to one rounding of the sum), then u * sx c.
+__device__ __forceinline__ float2 cmul_45(float2 a, float sx, float sy, float ch, float cl) {
+    const float sg = sy * sx;
+    const float2 u = f2_fma(make_float2(a.y, a.x), make_float2(-sg, sg), a);
+    return f2_fma(u, make_float2(sx * ch, sx * ch), f2_mul(u, make_float2(sx * cl, sx * cl)));
+}
+
 // a * W_R^K with W_R = exp(-2 pi i / R) (forward) or exp(+2 pi i / R) (inverse); R | 32.
 template <int K, int R, bool INV>
 __device__ __forceinline__ float2 twc(float2 a) {
@@ -70,11 +118,16 @@ __device__ __forceinline__ float2 twc(float2 a) {
         return make_float2(-a.x, -a.y);
     } else if constexpr (J == 24) {
         return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    } else if constexpr (J % 8 == 4) {
+        constexpr float sx = kCos32[J] > 0.f ? 1.f : -1.f;
+        constexpr float sy = ((INV ? kSin32[J] : -kSin32[J]) > 0.f) ? 1.f : -1.f;
+        constexpr float ch = kCos32[4], cl = kCos32Lo[4];
+        return cmul_45(a, sx, sy, ch, cl);
     } else {
         constexpr float c = kCos32[J], cl = kCos32Lo[J];
         constexpr float s = INV ? kSin32[J] : -kSin32[J];
         constexpr float sl = INV ? kSin32Lo[J] : -kSin32Lo[J];
-        return cmul_c(a, make_float2(c, s), make_float2(cl, sl));
+        return cmul_k(a, c, s, cl, sl);
     }
 }
 
@@ -82,9 +135,20 @@ template <int R, bool INV, int K = 0>
 struct Combine {
     __device__ __forceinline__ static void run(float2* v, const float2* e, const float2* o) {
         if constexpr (K < R / 2) {
-            const float2 t = twc<K, R, INV>(o[K]);
-            v[K] = cadd(e[K], t);
-            v[K + R / 2] = csub(e[K], t);
+            constexpr int J = (K * (32 / R)) % 32;
+            if constexpr (J == 8 || J == 24) {
+                // a rotation by +-i is a swap and a sign: fold it into scalar additions
+                const float2 t = twc<K, R, INV>(o[K]);
+                v[K] = make_float2(e[K].x + t.x, e[K].y + t.y);
+                v[K + R / 2] = make_float2(e[K].x - t.x, e[K].y - t.y);
+            } else if constexpr (J == 16) {
+                v[K] = csub(e[K], o[K]);
+                v[K + R / 2] = cadd(e[K], o[K]);
+            } else {
+                const float2 t = twc<K, R, INV>(o[K]);
+                v[K] = cadd(e[K], t);
+                v[K + R / 2] = csub(e[K], t);
+            }
             Combine<R, INV, K + 1>::run(v, e, o);
         }
     }
@@ -121,11 +185,7 @@ TWA_PLAN(8, 8, 1, 8)
 TWA_PLAN(16, 16, 1, 16)
 TWA_PLAN(32, 16, 2, 16, 2)
 TWA_PLAN(64, 8, 2, 8, 8)
-#ifdef TWA_PLAN128_R8
-TWA_PLAN(128, 8, 3, 8, 8, 2)
-#else
 TWA_PLAN(128, 16, 2, 16, 8)
-#endif
 TWA_PLAN(256, 16, 2, 16, 16)
 TWA_PLAN(512, 16, 3, 16, 8, 4)
 TWA_PLAN(1024, 16, 3, 16, 16, 4)

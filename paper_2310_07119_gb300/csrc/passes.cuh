@@ -86,10 +86,7 @@ __device__ __forceinline__ float2 kick_w(float2 z, float k_hi, float k_lo, float
 
 // At least 512 resident threads (16 warps) per SM so that one CTA's loads overlap another's
 // transforms; this caps the registers per thread at 128.
-#ifndef TWA_MIN_THREADS
-#define TWA_MIN_THREADS 512
-#endif
-constexpr int min_ctas(int threads) { return threads >= TWA_MIN_THREADS ? 1 : TWA_MIN_THREADS / threads; }
+constexpr int min_ctas(int threads) { return threads >= 512 ? 1 : 512 / threads; }
 
 // Ops that keep a per-thread array across the two streams of a pair park it in a thread-private
 // shared-memory stash (RMAX float2 per thread, after the exchange lines) instead of registers.
