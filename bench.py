@@ -225,6 +225,35 @@ def _cufft_reference_rate(w, batch=32, steps=5):
     return batch * m ** 3 * steps / (e0.elapsed_time(e1) * 1e-3)
 
 
+def _uneven_rate(steps=3):
+    """Uneven multi-instance batch in one handle (2D two-soliton merger: 512^2 x 128, 1024^2 x 64 and
+    2048^2 x 16 streams), moments every 10 steps, the instances on parallel graph branches."""
+    import tempfile
+    import torch
+    import twa_inputs as ti
+    from paper_2310_07119_gb300 import Ensemble, twa_advance
+    ws = [ti.workload_2d_merger(m, nr, 1000) for m, nr in ((512, 128), (1024, 64), (2048, 16))]
+    p = ws[0].phys
+    ens = Ensemble([w.grid for w in ws], p.hbar_m, p.C, p.dt, p.n_tot, [w.n_real for w in ws], want_modes=True)
+    ens.autotune(os.path.join(tempfile.gettempdir(), "twa_tune_cache.json"))
+    ens.sample([w.psi_cl() for w in ws], SEED)
+    warm = ens.new_series(2 * OUT_EVERY, OUT_EVERY)
+    twa_advance(ens.h, ens.psi, 2 * OUT_EVERY, OUT_EVERY, warm)
+    series = ens.new_series(steps * OUT_EVERY, OUT_EVERY)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    twa_advance(ens.h, ens.psi, steps * OUT_EVERY, OUT_EVERY, series)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ens.close()
+    cu = sum(w.n_real * w.grid.cells for w in ws) * OUT_EVERY * steps
+    return {"value": cu / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "workload": "2D two-soliton merger 512^2 x 128 + 1024^2 x 64 + 2048^2 x 16 streams in one handle, "
+                        f"{OUT_EVERY} KDK steps + moments per step, batch {sum((w.n_real + 1) * w.grid.cells for w in ws) * 8 / 1e9:.2f} GB"}
+
+
 def _e2e(ens, w, steps=2, n_run=50):
     """twa_run from a pinned host psi_cl to the host series, copies inside the timed region."""
     import torch
@@ -344,6 +373,8 @@ def run_twa(args):
         line["cufft_reference"] = {"value": _cufft_reference_rate(w), "unit": UNIT,
                                    "path": "torch.fft (cuFFT) KDK step, 32 fields, reference only"}
         cv, n, el = _oracle_rate(w)
+        line["uneven_batch"] = _uneven_rate()
+        torch.cuda.empty_cache()
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                                 "sample": f"2 streams of the 128^3 workload, {n} KDK steps in {el:.1f} s (FP64 scipy.fft)"}
     if rank == 0:

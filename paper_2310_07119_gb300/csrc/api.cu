@@ -87,6 +87,10 @@ struct twa_handle {
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     cudaGraphExec_t gexec = nullptr;
     long long graph_launches = 0;
+    // one stream and join event per instance, for the fork/join of multi-instance batches
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_ev;
+    cudaEvent_t ev_fork = nullptr;
     const void* g_psi = nullptr;
     const void* g_series = nullptr;
     int g_out_every = -1;
@@ -480,6 +484,45 @@ int closing_kick(twa_handle* h, Inst& I, float2* psi, double frac, cudaStream_t 
 }
 
 // Moments with a pending kick (0 for a synchronized batch); scalars into `scalars` (device).
+// Instances of a batch are independent.  With more than one, each instance's work goes to its own
+// stream between a fork on st and a join back onto st (inside a capture this makes parallel graph
+// branches), so the last wave of one instance's pass overlaps the passes of the others and an
+// uneven batch keeps the GPU full.  The pass profiler times passes one at a time and keeps st.
+struct Fork {
+    twa_handle* h;
+    cudaStream_t st;
+    bool on;
+    int open(size_t n) {
+        on = n > 1 && !h->prof_on;
+        if (!on) return 0;
+        while (h->side.size() < n) {
+            cudaStream_t x;
+            cudaEvent_t e;
+            CU(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+            h->side.push_back(x);
+            CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            h->side_ev.push_back(e);
+        }
+        if (!h->ev_fork) CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CU(cudaEventRecord(h->ev_fork, st));
+        return 0;
+    }
+    // stream of instance i (waits for the fork)
+    int stream(size_t i, cudaStream_t* out) {
+        *out = st;
+        if (!on) return 0;
+        CU(cudaStreamWaitEvent(h->side[i], h->ev_fork, 0));
+        *out = h->side[i];
+        return 0;
+    }
+    int join(size_t i) {
+        if (!on) return 0;
+        CU(cudaEventRecord(h->side_ev[i], h->side[i]));
+        CU(cudaStreamWaitEvent(st, h->side_ev[i], 0));
+        return 0;
+    }
+};
+
 int moments_f32(twa_handle* h, Inst& I, float2* psi, double pend, const twa_moments_out* o, double* scalars,
                 cudaStream_t st) {
     const bool v_spec = (I.mode == MODE_3D) && pend != 0.0;
@@ -747,6 +790,9 @@ int twa_destroy(twa_handle* h) {
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->ev_a) cudaEventDestroy(h->ev_a);
     if (h->ev_b) cudaEventDestroy(h->ev_b);
+    for (cudaStream_t x : h->side) cudaStreamDestroy(x);
+    for (cudaEvent_t e : h->side_ev) cudaEventDestroy(e);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     for (void* p : h->allocs) cudaFree(p);
     delete h;
     return TWA_OK;
@@ -787,15 +833,21 @@ int twa_step_batch(twa_handle* h, void* psi, int n_steps, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     h->launches = 0;
     if (n_steps == 0) return TWA_OK;
-    for (auto& I : h->in) {
+    Fork fk{h, st, false};
+    RC(fk.open(h->in.size()));
+    for (size_t i = 0; i < h->in.size(); ++i) {
+        Inst& I = h->in[i];
+        cudaStream_t s;
+        RC(fk.stream(i, &s));
         if (h->p.precision == TWA_F32) {
             float2* f = inst_psi(I, psi);
-            RC(poisson_init(h, I, f, st));
-            RC(steps_f32(h, I, f, n_steps, 0.5, st));
-            RC(closing_kick(h, I, f, 0.5, st));
+            RC(poisson_init(h, I, f, s));
+            RC(steps_f32(h, I, f, n_steps, 0.5, s));
+            RC(closing_kick(h, I, f, 0.5, s));
         } else {
-            RC(step_batch_f64(h, I, static_cast<double2*>(psi) + I.off, n_steps, st));
+            RC(step_batch_f64(h, I, static_cast<double2*>(psi) + I.off, n_steps, s));
         }
+        RC(fk.join(i));
     }
     CU(cudaGetLastError());
     return TWA_OK;
@@ -822,11 +874,16 @@ namespace {
 
 // One output interval of the FP32 run for all instances: steps, moments (pending half kick), store.
 int run_interval_f32(twa_handle* h, void* psi, int out_every, double a_first, double* series, cudaStream_t st) {
+    Fork fk{h, st, false};
+    RC(fk.open(h->in.size()));
     for (size_t i = 0; i < h->in.size(); ++i) {
         Inst& I = h->in[i];
         float2* f = inst_psi(I, psi);
-        RC(steps_f32(h, I, f, out_every, a_first, st));
-        RC(moments_f32(h, I, f, 0.5, nullptr, h->d_cur + i * TWA_NSCALARS, st));
+        cudaStream_t s;
+        RC(fk.stream(i, &s));
+        RC(steps_f32(h, I, f, out_every, a_first, s));
+        RC(moments_f32(h, I, f, 0.5, nullptr, h->d_cur + i * TWA_NSCALARS, s));
+        RC(fk.join(i));
     }
     launch_store_series(h->d_cur, series, h->d_counter, (int)h->in.size() * TWA_NSCALARS, st);
     ++h->launches;

@@ -184,6 +184,35 @@ def test_uneven_multi_instance_batch():
         assert np.all(field_rel_l2(got, ref, 2) < F32_FIELD_TOL)
 
 
+def test_forked_instances_match_serial_run_and_oracle():
+    """A three-instance uneven batch runs each instance on its own graph branch; the result is
+    bitwise the same as the serial run (the pass profiler keeps one stream) and matches the oracle."""
+    from paper_2310_07119_gb300 import twa_profile_enable
+    base = ti.small_workload("merger2d", 2, 64, 4, 30, n_tot=1e9, out_every=10, dt=DT_2D)
+    ws = [base]
+    for m, nr in ((32, 3), (128, 2)):
+        g = ti.Grid.cube(2, m)
+        ws.append(ti.Workload(base.name, g, base.phys, nr, base.n_steps, base.out_every, base.psi_cl_seed, base.noise_seed))
+    cls = [w.psi_cl() for w in ws]
+    out = []
+    for serial in (True, False):
+        ens = make_ensemble(ws, 0)
+        twa_profile_enable(ens.h, serial)
+        series = ens.run(cls, base.noise_seed, base.n_steps, base.out_every).cpu().numpy()
+        out.append((series, [ens.fields(i).cpu().numpy().copy() for i in range(len(ws))]))
+        ens.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
+    for i, w in enumerate(ws):
+        b0 = twa.sample(cls[i], w.noise_seed, w.n_real, w.phys.n_tot, w.grid.dV, w.phys.noise_conv, i)
+        _, ref_series, ref_final = twa.run(cls[i], w.phys.hbar_m, w.phys.C, w.phys.dt, w.grid.L, 2, w.phys.n_tot,
+                                           w.n_real, w.noise_seed, w.n_steps, w.out_every, batch=b0)
+        assert np.all(field_rel_l2(out[1][1][i].astype(np.complex128), ref_final, 2) < F32_FIELD_TOL)
+        for o, mo in enumerate(ref_series):
+            assert abs(out[1][0][o, i, 1] - mo["corr"]) <= CORR_TOL * mo["corr"] + 1e-12
+
+
 def test_streams_are_independent_of_batch_size():
     # slots keep their Poisson partner (2p, 2p+1) when the batch grows, so results are bitwise equal
     base = ti.small_workload("kgauss", 3, 16, 3, 10, n_tot=1e8)
@@ -269,6 +298,34 @@ def test_bench_size_sampled_realizations():
     assert np.all(rho_err < RHO_TOL), rho_err
 
 
+
+
+def test_uneven_2d_mix_full_size_sampled():
+    """The uneven 2D batch at its full layout (two-soliton merger, 512^2 x 128 + 1024^2 x 64 +
+    2048^2 x 16 streams in one handle, forked per instance), 10 KDK steps: the classical field and
+    two sampled streams of every instance against the oracle."""
+    from oracle.philox import wigner_normals
+    ws = [ti.workload_2d_merger(m, nr, 10) for m, nr in ((512, 128), (1024, 64), (2048, 16))]
+    cls = [w.psi_cl() for w in ws]
+    seed = ws[0].noise_seed
+    ens = make_ensemble(ws, 0, want_modes=False)
+    ens.sample(cls, seed)
+    ens.step(10)
+    for i, w in enumerate(ws):
+        slots = [0, 1, w.n_real]
+        sub = ens.fields(i)[slots].cpu().numpy().astype(np.complex128)
+        sig = twa.noise_sigma(w.phys.n_tot, w.grid.dV)
+        ref = np.empty((len(slots),) + cls[i].shape, dtype=np.complex128)
+        for j, sl in enumerate(slots):
+            if sl == 0:
+                ref[j] = cls[i]
+            else:
+                zr, zi = wigner_normals(seed, cls[i].size, sl, i)
+                ref[j] = cls[i] + sig * (zr + 1j * zi).reshape(cls[i].shape)
+        for _ in range(10):
+            ref = sp.step(ref, w.phys.hbar_m, w.phys.C, w.phys.dt, 1.0, 2)
+        assert np.all(field_rel_l2(sub, ref, 2) < F32_FIELD_TOL), (i, field_rel_l2(sub, ref, 2))
+    ens.close()
 
 PIPE = 1 << 16     # flag on a pass's "lines" value selecting its cp.async-pipelined variant
 PIPE_OPS = (0, 1, 2, 3, 5, 6, 7)     # drift, kick_drift, kick_drift_vinv, drift_rho, fwd, fwd_mul_inv, inv
