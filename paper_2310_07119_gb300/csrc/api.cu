@@ -211,6 +211,8 @@ int dispatch_pipe(int N, const LaunchCfg& c, const PassArgs& a, int tiles, int n
         case 128: return launch_pipe<128>(c, a, tiles, n_items, st, prep);
         case 256: return launch_pipe<256>(c, a, tiles, n_items, st, prep);
         case 512: return launch_pipe<512>(c, a, tiles, n_items, st, prep);
+        case 1024: return launch_pipe<1024>(c, a, tiles, n_items, st, prep);
+        case 2048: return launch_pipe<2048>(c, a, tiles, n_items, st, prep);
         default: return -1;
     }
 }
@@ -222,6 +224,8 @@ bool pipe_variant_ok(int N, int op, bool strided, int lines) {
         case 128: return has_pipe_variant<128>(op, strided, lines);
         case 256: return has_pipe_variant<256>(op, strided, lines);
         case 512: return has_pipe_variant<512>(op, strided, lines);
+        case 1024: return has_pipe_variant<1024>(op, strided, lines);
+        case 2048: return has_pipe_variant<2048>(op, strided, lines);
         default: return false;
     }
 }
@@ -649,11 +653,15 @@ int build_tables(twa_handle* h, Inst& I) {
             RC(upload(h, &I.ph[a], phf));
             RC(upload(h, &I.ph_lo[a], phl));
             if (a < I.dim && !h->tw32.count(n)) {
-                std::vector<float4> tw(n);
-                for (int j = 0; j < n; ++j) {
-                    const float hx = (float)twd[j].x, hy = (float)twd[j].y;
-                    tw[j] = make_float4(hx, hy, (float)(twd[j].x - (double)hx), (float)(twd[j].y - (double)hy));
+                // stage-major table of W_n^m (m from the plan's stage layout), hi + lo
+                std::vector<float4> tw;
+                for (int e = 0; tw_exponent_n(n, e) >= 0; ++e) {
+                    const int m = tw_exponent_n(n, e);
+                    const double c = twd[m].x, sv = twd[m].y;
+                    const float hx = (float)c, hy = (float)sv;
+                    tw.push_back(make_float4(hx, hy, (float)(c - (double)hx), (float)(sv - (double)hy)));
                 }
+                if (tw.empty()) tw.push_back(make_float4(1.f, 0.f, 0.f, 0.f));
                 float4* d = nullptr;
                 RC(upload(h, &d, tw));
                 h->tw32[n] = d;
@@ -1141,8 +1149,8 @@ int time_variant(twa_handle* h, Inst& I, float2* f, const TunePass& ps, int l, c
 
 int tune_passes(twa_handle* h, Inst& I, float2* f, const std::vector<TunePass>& passes, std::map<std::string, int>& cache,
                 cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-    const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512, PIPE_FLAG | 4, PIPE_FLAG | 8, PIPE_FLAG | 16,
-                        PIPE_FLAG | 32, PIPE_FLAG | 64};
+    const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512, PIPE_FLAG | 1, PIPE_FLAG | 2, PIPE_FLAG | 4,
+                        PIPE_FLAG | 8, PIPE_FLAG | 16, PIPE_FLAG | 32, PIPE_FLAG | 64};
     for (const auto& ps : passes) {
         const int N = I.n[ps.axis == 3 ? 0 : ps.axis];
         auto ok = [&](int l) {

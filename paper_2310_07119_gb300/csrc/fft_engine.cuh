@@ -198,10 +198,15 @@ TWA_PLAN(2048, 16, 3, 16, 16, 8)
 __host__ __device__ constexpr int pad_n(int n, int i) {
     return (n == 64 || n == 128) ? i + (i >> 3) + (i >> 6) : i + (i >> 4);
 }
-// Shared-memory line stride.  Column passes (lanes = lines): odd, so 16 lanes of a 64-bit access
-// phase fall in distinct banks.  Row passes (lanes = positions, T < 16 threads per line): the lines
+// Shared-memory line stride.  Column passes (lanes = lines): with 16 or more lines per CTA, odd,
+// so the 16 lanes of a 64-bit access phase fall in distinct banks; with fewer lines (long lines,
+// few per CTA), congruent to 16 / lines modulo 16, so the lines of an access phase start in
+// disjoint windows of banks.  Row passes (lanes = positions, T < 16 threads per line): the lines
 // sharing an access phase start 2 T banks apart, so each uses its own window of banks.
-__host__ __device__ constexpr int line_stride(int n) { return (pad_n(n, n) & 1) ? pad_n(n, n) : pad_n(n, n) + 1; }
+__host__ __device__ constexpr int line_stride(int n, int lines = 16) {
+    return lines >= 16 ? ((pad_n(n, n) & 1) ? pad_n(n, n) : pad_n(n, n) + 1)
+                       : pad_n(n, n) + ((16 / lines - pad_n(n, n) % 16) % 16 + 16) % 16;
+}
 __host__ __device__ constexpr int line_stride_rows(int n, int t) {
     return (t >= 16) ? pad_n(n, n) : pad_n(n, n) + ((t - pad_n(n, n) % 16) % 16 + 16) % 16;
 }
@@ -218,6 +223,70 @@ struct StageInfo<N, INV, 0> {
     static constexpr int R = INV ? P::R[P::S - 1] : P::R[0];
     static constexpr int NS = 1;
 };
+
+// Twiddle table of length-N transforms, stage-major: for the forward and then the inverse stage
+// order, every stage s >= 1 (radix R, sub-transform length NS) holds (R - 1) x NS entries
+// W_N^(r k N / (NS R)), r = 1..R-1 (rows), k = 0..NS-1 (consecutive), as float4 (hi.re, hi.im,
+// lo.re, lo.im).  Consecutive threads of a stage read consecutive entries.  tw_exponent gives the
+// power of W_N = exp(-2 pi i / N) stored at an index (-1 past the end).
+// radix s of the forward stage order (1 past the last stage); a constant expression, so device code
+// may use it at run time
+template <int N, int s>
+__host__ __device__ constexpr int plan_radix() {
+    if constexpr (s < Plan<N>::S) return Plan<N>::R[s];
+    else return 1;
+}
+template <int N>
+__host__ __device__ constexpr int tw_exponent(int idx) {
+    constexpr int S = Plan<N>::S;
+    const int Rf[3] = {plan_radix<N, 0>(), plan_radix<N, 1>(), plan_radix<N, 2>()};
+    for (int dir = 0; dir < 2; ++dir) {
+        int ns = 1;
+        for (int st = 0; st < S; ++st) {
+            const int R = dir ? Rf[S - 1 - st] : Rf[st];
+            if (st > 0) {
+                const int cnt = (R - 1) * ns;
+                if (idx < cnt) return ((idx / ns + 1) * (idx % ns) * (N / (ns * R))) % N;
+                idx -= cnt;
+            }
+            ns *= R;
+        }
+    }
+    return -1;
+}
+// first entry of stage s of the forward (INV = false) or inverse stage order
+template <int N, bool INV, int s>
+__host__ __device__ constexpr int tw_offset() {
+    constexpr int S = Plan<N>::S;
+    const int Rf[3] = {plan_radix<N, 0>(), plan_radix<N, 1>(), plan_radix<N, 2>()};
+    int off = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+        int ns = 1;
+        for (int st = 0; st < S; ++st) {
+            const int R = dir ? Rf[S - 1 - st] : Rf[st];
+            if (dir == (INV ? 1 : 0) && st == s) return off;
+            if (st > 0) off += (R - 1) * ns;
+            ns *= R;
+        }
+    }
+    return -1;
+}
+
+// tw_exponent for a run-time length (table builders); -1 for lengths without a plan
+__host__ __device__ inline int tw_exponent_n(int n, int idx) {
+    switch (n) {
+        case 8: return tw_exponent<8>(idx);
+        case 16: return tw_exponent<16>(idx);
+        case 32: return tw_exponent<32>(idx);
+        case 64: return tw_exponent<64>(idx);
+        case 128: return tw_exponent<128>(idx);
+        case 256: return tw_exponent<256>(idx);
+        case 512: return tw_exponent<512>(idx);
+        case 1024: return tw_exponent<1024>(idx);
+        case 2048: return tw_exponent<2048>(idx);
+        default: return -1;
+    }
+}
 
 // Position along the line of register slot `slot` in the natural layout (forward input,
 // inverse output) and in the spectral layout (forward output, inverse input).
@@ -248,6 +317,7 @@ struct FftStage {
     static constexpr int RMAX = P::RMAX, T = P::T, S = P::S;
     using SI = StageInfo<N, INV, s>;
     static constexpr int R = SI::R, NS = SI::NS;
+    static constexpr int TWO = tw_offset<N, INV, s>();  // this stage's block of the twiddle table
 
     __device__ __forceinline__ static void run(float2 (&v)[RMAX], int t, float2* sm, const float4* __restrict__ tw) {
         constexpr int B = RMAX / R;
@@ -258,7 +328,7 @@ struct FftStage {
                 const int k = j & (NS - 1);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float4 w = __ldg(&tw[(r * k) * (N / (NS * R))]);
+                    const float4 w = __ldg(&tw[TWO + (r - 1) * NS + k]);
                     v[b * R + r] = INV ? cmul_c(v[b * R + r], make_float2(w.x, -w.y), make_float2(w.z, -w.w))
                                        : cmul_c(v[b * R + r], make_float2(w.x, w.y), make_float2(w.z, w.w));
                 }

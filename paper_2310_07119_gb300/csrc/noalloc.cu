@@ -31,7 +31,7 @@ constexpr int kMaxN = 2048;
 constexpr long long kScratchElems = TWA_STATIC_SCRATCH_ELEMS;  // pairs * N complex values
 
 static __device__ __align__(256) float2 g_scratch[kScratchElems];
-static __device__ __align__(256) float4 g_tw[kMaxN];
+static __device__ __align__(256) float4 g_tw[2 * kMaxN];  // stage-major twiddles (< 2 N entries)
 static __device__ __align__(256) float2 g_ph[kMaxN];
 static __device__ __align__(256) float2 g_ph_lo[kMaxN];
 static __device__ __align__(256) float g_k2[kMaxN];
@@ -50,15 +50,19 @@ constexpr int kMaxDevices = 64;
 DevSyms g_dev[kMaxDevices];
 std::mutex g_mu;
 
-// Twiddles exp(-2 pi i j / N), kinetic phases exp(-i hbar k^2 dt / 2) / N (phase reduced mod 2 pi
+// Twiddles exp(-2 pi i m / N) in the stage-major layout of the transforms, kinetic phases exp(-i hbar k^2 dt / 2) / N (phase reduced mod 2 pi
 // in FP64) and k^2, each table entry split into float hi + lo, computed on the device in FP64.
 __global__ void k_tables_1d(float4* tw, float2* ph, float2* ph_lo, float* k2, float* zero, int n, double L,
                             double hbar, double dt) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
+        const int m = tw_exponent_n(n, e);
+        if (m < 0) continue;
         double s, c;
-        sincospi(-2.0 * (double)j / (double)n, &s, &c);
+        sincospi(-2.0 * (double)m / (double)n, &s, &c);
         const float cx = (float)c, sy = (float)s;
-        tw[j] = make_float4(cx, sy, (float)(c - (double)cx), (float)(s - (double)sy));
+        tw[e] = make_float4(cx, sy, (float)(c - (double)cx), (float)(s - (double)sy));
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const int m = (j < n / 2) ? j : j - n;
         const double k = 6.283185307179586476925286766559 * (double)m / L;
         const double th = fmod(hbar * k * k * dt * 0.5, 6.283185307179586476925286766559);

@@ -98,7 +98,7 @@ template <int N, int LINES, bool STRIDED, int OP>
 __global__ void __launch_bounds__(LINES * Plan<N>::T, (OP == OP_STEPS_1D) ? 1 : min_ctas(LINES * Plan<N>::T))
 k_line(const PassArgs a) {
     using P = Plan<N>;
-    constexpr int T = P::T, RMAX = P::RMAX, LS = STRIDED ? line_stride(N) : line_stride_rows(N, T);
+    constexpr int T = P::T, RMAX = P::RMAX, LS = STRIDED ? line_stride(N, LINES) : line_stride_rows(N, T);
     constexpr bool WARP = !STRIDED && (T <= 32);
     constexpr unsigned MASK = (LINES * T >= 32) ? 0xffffffffu : ((1u << (LINES * T)) - 1u);
     extern __shared__ float2 smem[];
@@ -130,9 +130,11 @@ k_line(const PassArgs a) {
     const int f = blockIdx.y;
     float2 v[RMAX];
 
+    // field data is read once per pass: load it through L2 only (ld.global.cg), so the twiddle,
+    // phase and k^2 tables keep the L1 cache
     auto load_nat = [&](float2 (&w)[RMAX], const float2* F) {
 #pragma unroll
-        for (int i = 0; i < RMAX; ++i) w[i] = F[base + pos_nat<N>(t, i) * S];
+        for (int i = 0; i < RMAX; ++i) w[i] = __ldcg(&F[base + pos_nat<N>(t, i) * S]);
     };
     auto store_nat = [&](const float2 (&w)[RMAX], float2* F) {
         if (!act) return;
@@ -141,7 +143,7 @@ k_line(const PassArgs a) {
     };
     auto load_spec = [&](float2 (&w)[RMAX], const float2* F) {
 #pragma unroll
-        for (int i = 0; i < RMAX; ++i) w[i] = F[base + pos_spec<N>(t, i) * S];
+        for (int i = 0; i < RMAX; ++i) w[i] = __ldcg(&F[base + pos_spec<N>(t, i) * S]);
     };
     auto store_spec = [&](const float2 (&w)[RMAX], float2* F) {
         if (!act) return;
@@ -188,8 +190,8 @@ k_line(const PassArgs a) {
 #pragma unroll
                 for (int i = 0; i < RMAX; ++i) {
                     const int e = base + pos_nat<N>(t, i) * S;
-                    const float2 c = VC[e];
-                    v[i] = kick_w(F[e], a.kick, a.kick_lo, h ? c.y : c.x);
+                    const float2 c = __ldcg(&VC[e]);
+                    v[i] = kick_w(__ldcg(&F[e]), a.kick, a.kick_lo, h ? c.y : c.x);
                 }
             } else {
                 load_nat(v, F);
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(L * Plan<N>::T, min_ctas(L * Plan<N>::T))
 k_plane(const PassArgs a) {
     using P = Plan<N>;
     constexpr int T = P::T, RMAX = P::RMAX;
-    constexpr int LSR = line_stride_rows(N, T), LSC = line_stride(N);
+    constexpr int LSR = line_stride_rows(N, T), LSC = line_stride(N, L);
     constexpr bool WARP = (T <= 32);
     constexpr unsigned MASK = (L * T >= 32) ? 0xffffffffu : ((1u << (L * T)) - 1u);
     extern __shared__ float2 smem[];

@@ -35,7 +35,7 @@ __host__ __device__ constexpr bool pipe_stash(int op) { return pipe_loads(op) > 
 template <int N, int LINES, bool STRIDED>
 __host__ __device__ constexpr int pipe_stage_elems() {
     constexpr int T = Plan<N>::T;
-    constexpr int ex = LINES * (STRIDED ? line_stride(N) : line_stride_rows(N, T));
+    constexpr int ex = LINES * (STRIDED ? line_stride(N, LINES) : line_stride_rows(N, T));
     constexpr int raw = STRIDED ? LINES * N : LINES * line_stride_rows(N, T);
     return ((ex > raw ? ex : raw) + 1) / 2 * 2;
 }
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(LINES * Plan<N>::T, min_ctas(LINES * Plan<N>::
 k_pipe(const PassArgs a, int tiles, int n_items) {
     using P = Plan<N>;
     constexpr int T = P::T, RMAX = P::RMAX, NTH = LINES * T;
-    constexpr int LS = STRIDED ? line_stride(N) : line_stride_rows(N, T);
+    constexpr int LS = STRIDED ? line_stride(N, LINES) : line_stride_rows(N, T);
     constexpr int RS = line_stride_rows(N, T);      // row stride of a contiguous raw tile
     constexpr bool WARP = !STRIDED && (T <= 32);
     constexpr unsigned MASK = (NTH >= 32) ? 0xffffffffu : ((1u << NTH) - 1u);

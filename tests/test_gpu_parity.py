@@ -329,7 +329,7 @@ def test_uneven_2d_mix_full_size_sampled():
 
 PIPE = 1 << 16     # flag on a pass's "lines" value selecting its cp.async-pipelined variant
 PIPE_OPS = (0, 1, 2, 3, 5, 6, 7)     # drift, kick_drift, kick_drift_vinv, drift_rho, fwd, fwd_mul_inv, inv
-THREADS_PER_LINE = {32: 2, 64: 8, 128: 8, 256: 16, 512: 32}    # N / registers-per-thread of the line FFT
+THREADS_PER_LINE = {32: 2, 64: 8, 128: 8, 256: 16, 512: 32, 1024: 64, 2048: 128}    # N / registers-per-thread of the line FFT
 
 
 def _force_pipelined(w, path, axis_pipeline):
@@ -351,7 +351,8 @@ RUN_PASSES = {"3d_axis": [(0, 2), (1, 0), (2, 3), (0, 5), (1, 6), (2, 7)], "3d_p
               "2d": [(0, 1), (1, 3), (0, 6), (1, 7)]}
 
 
-@pytest.mark.parametrize("name,axis_pipeline", [("3d_kgauss64", True), ("3d_kgauss64", False), ("2d_merger64", True)])
+@pytest.mark.parametrize("name,axis_pipeline", [("3d_kgauss64", True), ("3d_kgauss64", False), ("2d_merger64", True),
+                                                ("2d_merger2048", True)])
 def test_pipelined_passes_match_oracle(name, axis_pipeline, tmp_path):
     """The pipelined line passes, forced through the autotune cache, against the oracle (the cache
     the tuner writes back shows that it kept the pipelined variant of every pass the step runs)."""
@@ -359,8 +360,11 @@ def test_pipelined_passes_match_oracle(name, axis_pipeline, tmp_path):
     if name == "3d_kgauss64":
         w = ti.small_workload("kgauss", 3, 64, 3, 40, n_tot=1e8, dt=DT_128)
         runs = RUN_PASSES["3d_axis" if axis_pipeline else "3d_plane"]
-    else:
+    elif name == "2d_merger64":
         w = ti.small_workload("merger2d", 2, 64, 5, 40, n_tot=1e9, dt=DT_2D)
+        runs = RUN_PASSES["2d"]
+    else:
+        w = ti.small_workload("merger2d", 2, 2048, 1, 8, n_tot=1e9, dt=DT_2D)
         runs = RUN_PASSES["2d"]
     path = str(tmp_path / "force_pipe.json")
     _force_pipelined(w, path, axis_pipeline)
