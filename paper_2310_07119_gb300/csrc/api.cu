@@ -51,8 +51,7 @@ struct Inst {
     // FP32 path
     float2* vc = nullptr;
     float2* spec = nullptr;
-    float2* ph[3] = {nullptr, nullptr, nullptr};
-    float2* ph_lo[3] = {nullptr, nullptr, nullptr};
+    float4* ph[3] = {nullptr, nullptr, nullptr};  // kinetic phase per axis, (hi, lo)
     float* k2[3] = {nullptr, nullptr, nullptr};
     double* part_r = nullptr;
     double* part_m = nullptr;
@@ -286,11 +285,11 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
     a.out = out;
     a.tw = h->tw32[N];
     a.ph = I.ph[axis];
-    a.ph_lo = I.ph_lo[axis];
     a.post = post;
     a.k2x = I.k2[0];
     a.k2y = I.k2[1];
     a.k2z = I.k2[2];
+    a.k2a = I.k2[axis];
     split_kick(h, I, kick_frac, a.kick, a.kick_lo);
     split_kick(h, I, 1.0, a.kick2, a.kick2_lo);
     a.cells = I.cells;
@@ -387,9 +386,7 @@ int run_plane(twa_handle* h, Inst& I, float2* psi, int pop, double kick_frac, cu
     a.buf = I.vc;
     a.tw = h->tw32[N];
     a.ph = I.ph[0];
-    a.ph_lo = I.ph_lo[0];
     a.ph2 = I.ph[1];
-    a.ph2_lo = I.ph_lo[1];
     a.k2x = I.k2[0];
     a.k2y = I.k2[1];
     a.k2z = I.k2[2];
@@ -650,8 +647,9 @@ int build_tables(twa_handle* h, Inst& I) {
         }
         if (h->p.precision == TWA_F32) {
             RC(upload(h, &I.k2[a], k2f));
-            RC(upload(h, &I.ph[a], phf));
-            RC(upload(h, &I.ph_lo[a], phl));
+            std::vector<float4> phc(n);
+            for (int j = 0; j < n; ++j) phc[j] = make_float4(phf[j].x, phf[j].y, phl[j].x, phl[j].y);
+            RC(upload(h, &I.ph[a], phc));
             if (a < I.dim && !h->tw32.count(n)) {
                 // stage-major table of W_n^m (m from the plan's stage layout), hi + lo
                 std::vector<float4> tw;

@@ -32,8 +32,7 @@ constexpr long long kScratchElems = TWA_STATIC_SCRATCH_ELEMS;  // pairs * N comp
 
 static __device__ __align__(256) float2 g_scratch[kScratchElems];
 static __device__ __align__(256) float4 g_tw[2 * kMaxN];  // stage-major twiddles (< 2 N entries)
-static __device__ __align__(256) float2 g_ph[kMaxN];
-static __device__ __align__(256) float2 g_ph_lo[kMaxN];
+static __device__ __align__(256) float4 g_ph[kMaxN];  // kinetic phase (hi, lo)
 static __device__ __align__(256) float g_k2[kMaxN];
 static __device__ __align__(256) float g_zero[4];
 
@@ -41,8 +40,7 @@ struct DevSyms {
     bool ready = false;
     float2* scratch = nullptr;
     float4* tw = nullptr;
-    float2* ph = nullptr;
-    float2* ph_lo = nullptr;
+    float4* ph = nullptr;
     float* k2 = nullptr;
     float* zero = nullptr;
 };
@@ -52,7 +50,7 @@ std::mutex g_mu;
 
 // Twiddles exp(-2 pi i m / N) in the stage-major layout of the transforms, kinetic phases exp(-i hbar k^2 dt / 2) / N (phase reduced mod 2 pi
 // in FP64) and k^2, each table entry split into float hi + lo, computed on the device in FP64.
-__global__ void k_tables_1d(float4* tw, float2* ph, float2* ph_lo, float* k2, float* zero, int n, double L,
+__global__ void k_tables_1d(float4* tw, float4* ph, float* k2, float* zero, int n, double L,
                             double hbar, double dt) {
     for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) {
         const int m = tw_exponent_n(n, e);
@@ -70,8 +68,7 @@ __global__ void k_tables_1d(float4* tw, float2* ph, float2* ph_lo, float* k2, fl
         sincos(th, &ps, &pc);
         const double re = pc / n, im = -ps / n;
         const float rh = (float)re, ih = (float)im;
-        ph[j] = make_float2(rh, ih);
-        ph_lo[j] = make_float2((float)(re - (double)rh), (float)(im - (double)ih));
+        ph[j] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
         k2[j] = (float)(k * k);
     }
     if (threadIdx.x < 4) zero[threadIdx.x] = 0.f;
@@ -138,7 +135,6 @@ extern "C" int twa_step_batch_1d_static(const twa_grid* grid, const twa_params* 
             if (cudaGetSymbolAddress((void**)&s.scratch, g_scratch) != cudaSuccess ||
                 cudaGetSymbolAddress((void**)&s.tw, g_tw) != cudaSuccess ||
                 cudaGetSymbolAddress((void**)&s.ph, g_ph) != cudaSuccess ||
-                cudaGetSymbolAddress((void**)&s.ph_lo, g_ph_lo) != cudaSuccess ||
                 cudaGetSymbolAddress((void**)&s.k2, g_k2) != cudaSuccess ||
                 cudaGetSymbolAddress((void**)&s.zero, g_zero) != cudaSuccess) {
                 cudaGetLastError();
@@ -150,7 +146,7 @@ extern "C" int twa_step_batch_1d_static(const twa_grid* grid, const twa_params* 
         d = g_dev[dev];
     }
     if (n_steps == 0) return TWA_OK;
-    k_tables_1d<<<1, 256, 0, st>>>(d.tw, d.ph, d.ph_lo, d.k2, d.zero, N, grid->L, p->hbar_m, p->dt);
+    k_tables_1d<<<1, 256, 0, st>>>(d.tw, d.ph, d.k2, d.zero, N, grid->L, p->hbar_m, p->dt);
     const long long cells = N;
     auto split = [&](double frac, float& hi, float& lo) {
         const double k = -frac * p->dt * p->C / (p->hbar_m * (double)cells);
@@ -162,8 +158,8 @@ extern "C" int twa_step_batch_1d_static(const twa_grid* grid, const twa_params* 
     a.buf = d.scratch;
     a.tw = d.tw;
     a.ph = d.ph;
-    a.ph_lo = d.ph_lo;
     a.k2x = d.k2;
+    a.k2a = d.k2;
     a.k2y = d.zero;
     a.k2z = d.zero;
     a.S = 1;

@@ -40,11 +40,12 @@ struct PassArgs {
     float2* buf;            // packed Poisson buffer (one field per pair) or a field buffer
     float2* out;            // destination of OP_KICK_FWD_OUT (one field per slot)
     const float4* tw;       // exp(-2 pi i m / N), m < N, as (hi.re, hi.im, lo.re, lo.im)
-    const float2* ph;       // exp(-i hbar k^2 dt / 2) / N along this axis, FFT order (float hi part)
-    const float2* ph_lo;    // the remainder (exact value - hi) rounded to float
+    const float4* ph;       // exp(-i hbar k^2 dt / 2) / N along this axis, FFT order: (hi.re, hi.im,
+                            // lo.re, lo.im), lo = the remainder (exact value - hi) rounded to float
     const float* k2x;       // k^2 tables per axis (FFT order; length 1 and 0 for unused axes)
     const float* k2y;
     const float* k2z;
+    const float* k2a;       // k^2 table of the pass's own axis (FFT order)
     float kick, kick_lo;    // -a dt C / (hbar cells) for the (first) kick, as hi + lo
     float kick2, kick2_lo;  // same with a = 1 for later kicks (OP_STEPS_1D)
     int S;                  // stride of the axis (elements)
@@ -56,8 +57,7 @@ struct PassArgs {
     int lx, lxy;            // log2 nx, log2 (nx ny)
     int nsteps;             // OP_STEPS_1D
     float post;             // OP_FWD: factor applied before the store (1, or 1/N to undo an inverse)
-    const float2* ph2;      // plane passes: kinetic phase along y (hi, lo)
-    const float2* ph2_lo;
+    const float4* ph2;      // plane passes: kinetic phase along y (hi, lo)
 };
 
 // z * exp(-i theta).  For |theta| <= 1/4 (every kick of the measured workloads) sin and cos are
@@ -89,7 +89,7 @@ __device__ __forceinline__ float2 kick_w(float2 z, float k_hi, float k_lo, float
 constexpr int min_ctas(int threads) { return threads >= 512 ? 1 : 512 / threads; }
 
 // Ops that keep a per-thread array across the two streams of a pair park it in a thread-private
-// shared-memory stash (RMAX float2 per thread, after the exchange lines) instead of registers.
+// shared-memory stash (2 RMAX floats per thread, after the exchange lines) instead of registers.
 constexpr bool op_stash(int op) {
     return op == OP_DRIFT_RHO || op == OP_RHO_FWD || op == OP_KICK_DRIFT_VINV || op == OP_KICK_VINV;
 }
@@ -108,7 +108,6 @@ k_line(const PassArgs a) {
     float2* sm = smem + l * LS;
     const float4* __restrict__ tw = a.tw;
     constexpr int NTH = LINES * T;
-    float2* stash = smem + LINES * LS + tid;     // stash[i * NTH]: slot i of this thread
 
     // Line of this thread (element offset of its first cell inside a field; a field has fewer
     // than 2^31 cells); lines past the end of the field (partial tiles of small grids) run on a
@@ -155,15 +154,18 @@ k_line(const PassArgs a) {
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
             const int k = pos_spec<N>(t, i);
-            w[i] = cmul_c(w[i], __ldg(&a.ph[k]), __ldg(&a.ph_lo[k]));
+            const float4 p = __ldg(&a.ph[k]);
+            w[i] = cmul_c(w[i], make_float2(p.x, p.y), make_float2(p.z, p.w));
         }
     };
+    // 1/k^2 (0 at k = 0): the k^2 of the two other axes is fixed along the line (read once at the
+    // line's first cell, where this axis' wavenumber is 0); this axis' k^2 is read per slot
     auto poisson = [&](float2 (&w)[RMAX]) {
         const int mx = (1 << a.lx) - 1, my = (1 << (a.lxy - a.lx)) - 1;
+        const float k2f = __ldg(&a.k2x[base & mx]) + __ldg(&a.k2y[(base >> a.lx) & my]) + __ldg(&a.k2z[base >> a.lxy]);
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
-            const int e = base + pos_spec<N>(t, i) * S;
-            const float k2 = __ldg(&a.k2x[e & mx]) + __ldg(&a.k2y[(e >> a.lx) & my]) + __ldg(&a.k2z[e >> a.lxy]);
+            const float k2 = k2f + __ldg(&a.k2a[pos_spec<N>(t, i)]);
             const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
             w[i] = make_float2(w[i].x * m, w[i].y * m);
         }
@@ -208,25 +210,29 @@ k_line(const PassArgs a) {
         // inverse transform of the pair's Poisson line, parked in the stash for both streams
         load_spec(v, a.buf + (long long)f * a.cells);
         fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+        // the two streams' potentials as separate float planes (each stream reads only its own)
+        float* stv = reinterpret_cast<float*>(smem + LINES * LS) + tid;
 #pragma unroll
-        for (int i = 0; i < RMAX; ++i) stash[i * NTH] = v[i];
+        for (int i = 0; i < RMAX; ++i) {
+            stv[i * NTH] = v[i].x;
+            stv[(RMAX + i) * NTH] = v[i].y;
+        }
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
             const int slot = 2 * f + h;
             if (slot >= a.n_slots) break;
             float2* F = a.psi + (long long)slot * a.cells;
             load_nat(v, F);
+            const float* sv = stv + h * RMAX * NTH;
 #pragma unroll
-            for (int i = 0; i < RMAX; ++i) {
-                const float2 w = stash[i * NTH];
-                v[i] = kick_w(v[i], a.kick, a.kick_lo, h ? w.y : w.x);
-            }
+            for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, sv[i * NTH]);
             if constexpr (OP == OP_KICK_DRIFT_VINV) drift(v);
             store_nat(v, F);
         }
     } else if constexpr (OP == OP_DRIFT_RHO || OP == OP_RHO_FWD) {
         // density of slot 2f parked in the stash while slot 2f+1 is processed, then packed as
         // rho_0 + i rho_1 in v and transformed (one loop body: no hoisting of the second stream)
+        float* sr = reinterpret_cast<float*>(smem + LINES * LS) + tid;  // density of slot 2f
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
             const int slot = 2 * f + h;
@@ -243,10 +249,10 @@ k_line(const PassArgs a) {
             }
             if (h == 0) {
 #pragma unroll
-                for (int i = 0; i < RMAX; ++i) stash[i * NTH].x = fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
+                for (int i = 0; i < RMAX; ++i) sr[i * NTH] = fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
             } else {
 #pragma unroll
-                for (int i = 0; i < RMAX; ++i) v[i] = make_float2(stash[i * NTH].x, fmaf(v[i].x, v[i].x, v[i].y * v[i].y));
+                for (int i = 0; i < RMAX; ++i) v[i] = make_float2(sr[i * NTH], fmaf(v[i].x, v[i].x, v[i].y * v[i].y));
             }
         }
         fft_line<N, false, WARP, MASK>(v, t, sm, tw);
@@ -358,11 +364,12 @@ k_plane(const PassArgs a) {
     const int f = blockIdx.y;
     float2 v[RMAX];
 
-    auto phase = [&](float2 (&w)[RMAX], const float2* ph, const float2* phl, int t) {
+    auto phase = [&](float2 (&w)[RMAX], const float4* ph, int t) {
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
             const int k = pos_spec<N>(t, i);
-            w[i] = cmul_c(w[i], __ldg(&ph[k]), __ldg(&phl[k]));
+            const float4 p = __ldg(&ph[k]);
+            w[i] = cmul_c(w[i], make_float2(p.x, p.y), make_float2(p.z, p.w));
         }
     };
     auto poisson = [&](float2 (&w)[RMAX], int col) {
@@ -394,7 +401,7 @@ k_plane(const PassArgs a) {
                     v[i] = kick_w(__ldcg(&F[e]), a.kick, a.kick_lo, h ? c.y : c.x);
                 }
                 fft_line<N, false, WARP, MASK>(v, tr, smr, tw);
-                phase(v, a.ph, a.ph_lo, tr);
+                phase(v, a.ph, tr);
                 fft_line<N, true, WARP, MASK>(v, tr, smr, tw);
 #pragma unroll
                 for (int i = 0; i < RMAX; ++i) F[row + pos_nat<N>(tr, i)] = v[i];
@@ -407,7 +414,7 @@ k_plane(const PassArgs a) {
 #pragma unroll
                 for (int i = 0; i < RMAX; ++i) v[i] = __ldcg(&F[col + pos_nat<N>(tc, i) * N]);
                 fft_line<N, false, false>(v, tc, smc, tw);
-                phase(v, a.ph2, a.ph2_lo, tc);
+                phase(v, a.ph2, tc);
                 fft_line<N, true, false>(v, tc, smc, tw);
 #pragma unroll
                 for (int i = 0; i < RMAX; ++i) F[col + pos_nat<N>(tc, i) * N] = v[i];

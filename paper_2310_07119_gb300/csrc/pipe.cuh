@@ -55,7 +55,7 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
     extern __shared__ __align__(16) float2 psm[];
     float2* stage0 = psm;
     float2* stage1 = psm + SE;
-    float2* stash = psm + 2 * SE + threadIdx.x;      // stash[i * NTH]
+    float* stf = reinterpret_cast<float*>(psm + 2 * SE) + threadIdx.x;  // per-thread stash, stf[i * NTH]
     const int tid = threadIdx.x;
     const int l = STRIDED ? (tid % LINES) : (tid / T);
     const int t = STRIDED ? (tid / LINES) : (tid % T);
@@ -143,7 +143,8 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) {
                 const int k = pos_spec<N>(t, i);
-                v[i] = cmul_c(v[i], __ldg(&a.ph[k]), __ldg(&a.ph_lo[k]));
+                const float4 p = __ldg(&a.ph[k]);
+                v[i] = cmul_c(v[i], make_float2(p.x, p.y), make_float2(p.z, p.w));
             }
             fft_line<N, true, WARP, MASK>(v, t, sm, tw);
         };
@@ -167,10 +168,10 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
             ld(false);
             fft_line<N, false, WARP, MASK>(v, t, sm, tw);
             const int mx = (1 << a.lx) - 1, my = (1 << (a.lxy - a.lx)) - 1;
+            const float k2f = __ldg(&a.k2x[base & mx]) + __ldg(&a.k2y[(base >> a.lx) & my]) + __ldg(&a.k2z[base >> a.lxy]);
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) {
-                const int e = base + pos_spec<N>(t, i) * S;
-                const float k2 = __ldg(&a.k2x[e & mx]) + __ldg(&a.k2y[(e >> a.lx) & my]) + __ldg(&a.k2z[e >> a.lxy]);
+                const float k2 = k2f + __ldg(&a.k2a[pos_spec<N>(t, i)]);
                 const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
                 v[i] = make_float2(v[i].x * m, v[i].y * m);
             }
@@ -188,11 +189,11 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
             }
             if (sub == 0) {
 #pragma unroll
-                for (int i = 0; i < RMAX; ++i) stash[i * NTH].x = fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
+                for (int i = 0; i < RMAX; ++i) stf[i * NTH] = fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
             } else {
 #pragma unroll
                 for (int i = 0; i < RMAX; ++i)
-                    v[i] = make_float2(stash[i * NTH].x, fmaf(v[i].x, v[i].x, v[i].y * v[i].y));
+                    v[i] = make_float2(stf[i * NTH], fmaf(v[i].x, v[i].x, v[i].y * v[i].y));
                 fft_line<N, false, WARP, MASK>(v, t, sm, tw);
                 st_spec(a.buf + (long long)f * a.cells);
             }
@@ -204,17 +205,19 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
                 } else {
                     ld(false);
                 }
+                float* stv = reinterpret_cast<float*>(psm + 2 * SE) + threadIdx.x;
 #pragma unroll
-                for (int i = 0; i < RMAX; ++i) stash[i * NTH] = v[i];
+                for (int i = 0; i < RMAX; ++i) {
+                    stv[i * NTH] = v[i].x;
+                    stv[(RMAX + i) * NTH] = v[i].y;
+                }
             } else {
                 const int slot = 2 * f + sub - 1;
                 if (slot < a.n_slots) {
                     ld(false);
+                    const float* sv = reinterpret_cast<const float*>(psm + 2 * SE) + threadIdx.x + (sub - 1) * RMAX * NTH;
 #pragma unroll
-                    for (int i = 0; i < RMAX; ++i) {
-                        const float2 w = stash[i * NTH];
-                        v[i] = kick_w(v[i], a.kick, a.kick_lo, sub == 2 ? w.y : w.x);
-                    }
+                    for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, sv[i * NTH]);
                     drift();
                     st_nat(a.psi + (long long)slot * a.cells);
                 }
