@@ -197,6 +197,31 @@ def shell_errors(pred: np.ndarray, ref: np.ndarray, grid: int, nbins: int):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def fallback_statistic(pred_corr: np.ndarray, est_corr: np.ndarray, grid: int, nbins: int) -> float:
+    """Disagreement of the surrogate with the few-stream estimate it was given: relative L2 distance
+    of their shell-averaged correction spectra (number units)."""
+    return shell_errors(pred_corr, est_corr, grid, nbins)
+
+
+def calibrate_fallback(stats: Sequence[float], quantile: float = 0.9) -> float:
+    """Threshold on the fallback statistic: its `quantile` over validation samples (runs where the
+    surrogate is trusted); above it, a prediction is replaced by a full-ensemble run."""
+    v = np.asarray(list(stats), dtype=np.float64)
+    if v.size == 0 or not np.all(np.isfinite(v)):
+        raise ValueError("calibrate_fallback: need finite validation statistics")
+    return float(np.quantile(v, quantile))
+
+
+def correct_or_fallback(pred_corr: np.ndarray, est_corr: np.ndarray, grid: int, nbins: int, tau: float):
+    """(correction, fell_back): the surrogate's correction when it agrees with the few-stream
+    estimate within the calibrated threshold tau; otherwise (None, True), and the caller runs the
+    full ensemble for that snapshot."""
+    stat = fallback_statistic(pred_corr, est_corr, grid, nbins)
+    if not np.isfinite(stat) or stat > tau:
+        return None, True
+    return pred_corr, False
+
+
 def main(argv=None):
     """Train the surrogate on library-generated runs and report held-out errors (JSON lines).
 
