@@ -91,7 +91,8 @@ constexpr int min_ctas(int threads) { return threads >= 512 ? 1 : 512 / threads;
 // Ops that keep a per-thread array across the two streams of a pair park it in a thread-private
 // shared-memory stash (2 RMAX floats per thread, after the exchange lines) instead of registers.
 constexpr bool op_stash(int op) {
-    return op == OP_DRIFT_RHO || op == OP_RHO_FWD || op == OP_KICK_DRIFT_VINV || op == OP_KICK_VINV;
+    return op == OP_DRIFT_RHO || op == OP_RHO_FWD || op == OP_KICK_DRIFT_VINV || op == OP_KICK_VINV ||
+           op == OP_KICK_DRIFT || op == OP_KICK_FWD_OUT;
 }
 
 template <int N, int LINES, bool STRIDED, int OP>
@@ -182,21 +183,27 @@ k_line(const PassArgs a) {
         drift(v);
         store_nat(v, F);
     } else if constexpr (OP == OP_KICK_DRIFT || OP == OP_KICK_FWD_OUT) {
-        const float2* VC = a.buf + (long long)f * a.cells;
+        // the pair's real potentials are read once and parked in the stash as two float planes
+        float* stv = reinterpret_cast<float*>(smem + LINES * LS) + tid;
+        const bool kick = a.kick != 0.f;
+        if (kick) {
+            load_nat(v, a.buf + (long long)f * a.cells);
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) {
+                stv[i * NTH] = v[i].x;
+                stv[(RMAX + i) * NTH] = v[i].y;
+            }
+        }
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
             const int slot = 2 * f + h;
             if (slot >= a.n_slots) break;
             float2* F = a.psi + (long long)slot * a.cells;
-            if (a.kick != 0.f) {
+            load_nat(v, F);
+            if (kick) {
+                const float* sv = stv + h * RMAX * NTH;
 #pragma unroll
-                for (int i = 0; i < RMAX; ++i) {
-                    const int e = base + pos_nat<N>(t, i) * S;
-                    const float2 c = __ldcg(&VC[e]);
-                    v[i] = kick_w(__ldcg(&F[e]), a.kick, a.kick_lo, h ? c.y : c.x);
-                }
-            } else {
-                load_nat(v, F);
+                for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, sv[i * NTH]);
             }
             if constexpr (OP == OP_KICK_DRIFT) {
                 drift(v);
