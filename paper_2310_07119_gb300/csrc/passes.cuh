@@ -379,12 +379,12 @@ k_plane(const PassArgs a) {
             w[i] = cmul_c(w[i], make_float2(p.x, p.y), make_float2(p.z, p.w));
         }
     };
+    // columns run along y: k_x (the column) and k_z (the plane) are fixed, k_y is read per slot
     auto poisson = [&](float2 (&w)[RMAX], int col) {
-        const int mx = (1 << a.lx) - 1, my = (1 << (a.lxy - a.lx)) - 1;
+        const float k2f = __ldg(&a.k2x[col]) + __ldg(&a.k2z[blockIdx.x]);
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
-            const int e = plane + col + pos_spec<N>(tc, i) * N;
-            const float k2 = __ldg(&a.k2x[e & mx]) + __ldg(&a.k2y[(e >> a.lx) & my]) + __ldg(&a.k2z[e >> a.lxy]);
+            const float k2 = k2f + __ldg(&a.k2y[pos_spec<N>(tc, i)]);
             const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
             w[i] = make_float2(w[i].x * m, w[i].y * m);
         }
@@ -401,12 +401,15 @@ k_plane(const PassArgs a) {
 #pragma unroll 1
             for (int r0 = 0; r0 < N; r0 += L) {
                 const int row = (r0 + lr) * N;
+                // all loads first (the field, then this stream's potential component), then the kicks
+                const float* Wh = reinterpret_cast<const float*>(Wp) + h;
+                float w[RMAX];
 #pragma unroll
-                for (int i = 0; i < RMAX; ++i) {
-                    const int e = row + pos_nat<N>(tr, i);
-                    const float2 c = __ldcg(&Wp[e]);
-                    v[i] = kick_w(__ldcg(&F[e]), a.kick, a.kick_lo, h ? c.y : c.x);
-                }
+                for (int i = 0; i < RMAX; ++i) v[i] = __ldcg(&F[row + pos_nat<N>(tr, i)]);
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) w[i] = __ldcg(&Wh[2 * (row + pos_nat<N>(tr, i))]);
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, w[i]);
                 fft_line<N, false, WARP, MASK>(v, tr, smr, tw);
                 phase(v, a.ph, tr);
                 fft_line<N, true, WARP, MASK>(v, tr, smr, tw);
