@@ -272,6 +272,13 @@ __host__ __device__ constexpr int tw_offset() {
     return -1;
 }
 
+// number of entries of the table (a constant expression)
+template <int N>
+__host__ __device__ constexpr int tw_entries() {
+    int e = 0;
+    while (tw_exponent<N>(e) >= 0) ++e;
+    return e;
+}
 // tw_exponent for a run-time length (table builders); -1 for lengths without a plan
 __host__ __device__ inline int tw_exponent_n(int n, int idx) {
     switch (n) {
@@ -311,7 +318,7 @@ __device__ __forceinline__ void line_sync() {
     else __syncthreads();
 }
 
-template <int N, bool INV, int s, bool WARP, unsigned MASK>
+template <int N, bool INV, int s, bool WARP, unsigned MASK, bool TS = false>
 struct FftStage {
     using P = Plan<N>;
     static constexpr int RMAX = P::RMAX, T = P::T, S = P::S;
@@ -328,7 +335,8 @@ struct FftStage {
                 const int k = j & (NS - 1);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float4 w = __ldg(&tw[TWO + (r - 1) * NS + k]);
+                    // TS: the table is in shared memory; otherwise a read-only global load (L1)
+                    const float4 w = TS ? tw[TWO + (r - 1) * NS + k] : __ldg(&tw[TWO + (r - 1) * NS + k]);
                     v[b * R + r] = INV ? cmul_c(v[b * R + r], make_float2(w.x, -w.y), make_float2(w.z, -w.w))
                                        : cmul_c(v[b * R + r], make_float2(w.x, w.y), make_float2(w.z, w.w));
                 }
@@ -353,15 +361,15 @@ struct FftStage {
                 for (int r = 0; r < R2; ++r) v[b * R2 + r] = sm[pad_n(N, j + r * (N / R2))];
             }
             line_sync<WARP, MASK>();
-            FftStage<N, INV, s + 1, WARP, MASK>::run(v, t, sm, tw);
+            FftStage<N, INV, s + 1, WARP, MASK, TS>::run(v, t, sm, tw);
         }
     }
 };
 
 // Forward (INV = false) or inverse transform of one line held as in pos_nat / pos_spec.
-template <int N, bool INV, bool WARP, unsigned MASK = 0xffffffffu>
+template <int N, bool INV, bool WARP, unsigned MASK = 0xffffffffu, bool TS = false>
 __device__ __forceinline__ void fft_line(float2 (&v)[Plan<N>::RMAX], int t, float2* sm, const float4* __restrict__ tw) {
-    FftStage<N, INV, 0, WARP, MASK>::run(v, t, sm, tw);
+    FftStage<N, INV, 0, WARP, MASK, TS>::run(v, t, sm, tw);
 }
 
 }  // namespace twa

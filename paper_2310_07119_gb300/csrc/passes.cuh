@@ -90,7 +90,18 @@ constexpr int min_ctas(int threads) { return threads >= 512 ? 1 : 512 / threads;
 
 // Ops that keep a per-thread array across the two streams of a pair park it in a thread-private
 // shared-memory stash (2 RMAX floats per thread, after the exchange lines) instead of registers.
-constexpr bool op_stash(int op) {
+// The heavy pair passes (four or five transforms per CTA) of lengths 16..256 copy the twiddle table
+// and this axis' kinetic phases into shared memory once per CTA: the per-value table reads then skip
+// the L1 tag stage, which the streamed field accesses keep busy.  Lighter passes keep L1-cached
+// reads (the copy and its barrier would cost them more than it saves).
+template <int N, int OP>
+__host__ __device__ constexpr bool tables_in_smem() {
+    return N >= 16 && N <= 256 && (OP == OP_KICK_DRIFT_VINV || OP == OP_DRIFT_RHO || OP == OP_KICK_DRIFT);
+}
+template <int N, int OP>
+__host__ __device__ constexpr int smem_table_float4() { return tables_in_smem<N, OP>() ? tw_entries<N>() + N : 0; }
+
+__host__ __device__ constexpr bool op_stash(int op) {
     return op == OP_DRIFT_RHO || op == OP_RHO_FWD || op == OP_KICK_DRIFT_VINV || op == OP_KICK_VINV ||
            op == OP_KICK_DRIFT || op == OP_KICK_FWD_OUT;
 }
@@ -107,8 +118,19 @@ k_line(const PassArgs a) {
     const int l = STRIDED ? (tid % LINES) : (tid / T);
     const int t = STRIDED ? (tid / LINES) : (tid % T);
     float2* sm = smem + l * LS;
-    const float4* __restrict__ tw = a.tw;
     constexpr int NTH = LINES * T;
+    const float4* tw = a.tw;
+    const float4* ph = a.ph;
+    constexpr bool TS = tables_in_smem<N, OP>();
+    if constexpr (TS) {
+        constexpr int E = tw_entries<N>();
+        float4* st = reinterpret_cast<float4*>(smem + LINES * LS + (op_stash(OP) ? RMAX * NTH : 0));
+        for (int i = tid; i < E; i += NTH) st[i] = __ldg(&a.tw[i]);
+        for (int i = tid; i < N; i += NTH) st[E + i] = __ldg(&a.ph[i]);
+        __syncthreads();
+        tw = st;
+        ph = st + E;
+    }
 
     // Line of this thread (element offset of its first cell inside a field; a field has fewer
     // than 2^31 cells); lines past the end of the field (partial tiles of small grids) run on a
@@ -155,7 +177,7 @@ k_line(const PassArgs a) {
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
             const int k = pos_spec<N>(t, i);
-            const float4 p = __ldg(&a.ph[k]);
+            const float4 p = TS ? ph[k] : __ldg(&ph[k]);
             w[i] = cmul_c(w[i], make_float2(p.x, p.y), make_float2(p.z, p.w));
         }
     };
@@ -172,9 +194,9 @@ k_line(const PassArgs a) {
         }
     };
     auto drift = [&](float2 (&w)[RMAX]) {
-        fft_line<N, false, WARP, MASK>(w, t, sm, tw);
+        fft_line<N, false, WARP, MASK, TS>(w, t, sm, tw);
         phase(w);
-        fft_line<N, true, WARP, MASK>(w, t, sm, tw);
+        fft_line<N, true, WARP, MASK, TS>(w, t, sm, tw);
     };
 
     if constexpr (OP == OP_DRIFT) {
@@ -209,14 +231,14 @@ k_line(const PassArgs a) {
                 drift(v);
                 store_nat(v, F);
             } else {
-                fft_line<N, false, WARP, MASK>(v, t, sm, tw);
+                fft_line<N, false, WARP, MASK, TS>(v, t, sm, tw);
                 store_spec(v, a.out + (long long)slot * a.cells);
             }
         }
     } else if constexpr (OP == OP_KICK_DRIFT_VINV || OP == OP_KICK_VINV) {
         // inverse transform of the pair's Poisson line, parked in the stash for both streams
         load_spec(v, a.buf + (long long)f * a.cells);
-        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+        fft_line<N, true, WARP, MASK, TS>(v, t, sm, tw);
         // the two streams' potentials as separate float planes (each stream reads only its own)
         float* stv = reinterpret_cast<float*>(smem + LINES * LS) + tid;
 #pragma unroll
@@ -262,12 +284,12 @@ k_line(const PassArgs a) {
                 for (int i = 0; i < RMAX; ++i) v[i] = make_float2(sr[i * NTH], fmaf(v[i].x, v[i].x, v[i].y * v[i].y));
             }
         }
-        fft_line<N, false, WARP, MASK>(v, t, sm, tw);
+        fft_line<N, false, WARP, MASK, TS>(v, t, sm, tw);
         store_spec(v, a.buf + (long long)f * a.cells);
     } else if constexpr (OP == OP_FWD) {
         float2* F = a.buf + (long long)f * a.cells;
         load_nat(v, F);
-        fft_line<N, false, WARP, MASK>(v, t, sm, tw);
+        fft_line<N, false, WARP, MASK, TS>(v, t, sm, tw);
         if (a.post != 1.0f) {
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) v[i] = make_float2(v[i].x * a.post, v[i].y * a.post);
@@ -276,20 +298,20 @@ k_line(const PassArgs a) {
     } else if constexpr (OP == OP_FWD_MUL_INV) {
         float2* F = a.buf + (long long)f * a.cells;
         load_nat(v, F);
-        fft_line<N, false, WARP, MASK>(v, t, sm, tw);
+        fft_line<N, false, WARP, MASK, TS>(v, t, sm, tw);
         poisson(v);
-        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+        fft_line<N, true, WARP, MASK, TS>(v, t, sm, tw);
         store_nat(v, F);
     } else if constexpr (OP == OP_MUL_INV) {
         float2* F = a.buf + (long long)f * a.cells;
         load_spec(v, F);
         poisson(v);
-        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+        fft_line<N, true, WARP, MASK, TS>(v, t, sm, tw);
         store_nat(v, F);
     } else if constexpr (OP == OP_INV) {
         float2* F = a.buf + (long long)f * a.cells;
         load_spec(v, F);
-        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
+        fft_line<N, true, WARP, MASK, TS>(v, t, sm, tw);
         store_nat(v, F);
     } else if constexpr (OP == OP_STEPS_1D) {
         // base is the line offset inside the field; here each line slot of the CTA is one pair.
@@ -322,14 +344,14 @@ k_line(const PassArgs a) {
 #pragma unroll
             for (int i = 0; i < RMAX; ++i)
                 w[i] = make_float2(fmaf(v[i].x, v[i].x, v[i].y * v[i].y), fmaf(u1[i].x, u1[i].x, u1[i].y * u1[i].y));
-            fft_line<N, false, WARP, MASK>(w, t, sm, tw);
+            fft_line<N, false, WARP, MASK, TS>(w, t, sm, tw);
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) {
                 const float k2 = __ldg(&a.k2x[pos_spec<N>(t, i)]);
                 const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
                 w[i] = make_float2(w[i].x * m, w[i].y * m);
             }
-            fft_line<N, true, WARP, MASK>(w, t, sm, tw);
+            fft_line<N, true, WARP, MASK, TS>(w, t, sm, tw);
         }
         if (active) {
 #pragma unroll
