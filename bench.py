@@ -225,6 +225,31 @@ def _cufft_reference_rate(w, batch=32, steps=5):
     return batch * m ** 3 * steps / (e0.elapsed_time(e1) * 1e-3)
 
 
+def _one_d_rate():
+    """The 1D workload (256 cells, 32 streams + classical, 1000 KDK steps, moments every 10): one
+    on-chip launch per output interval on the FP32 path; the FP64 plain path on the same run."""
+    import torch
+    import twa_inputs as ti
+    from paper_2310_07119_gb300 import Ensemble, F32, F64_PLAIN, twa_advance
+    w = ti.workload_1d_bump(256, 32, 1000)
+    out = {}
+    for name, prec in (("f32", F32), ("f64_plain", F64_PLAIN)):
+        ens = Ensemble([w.grid], w.phys.hbar_m, w.phys.C, w.phys.dt, w.phys.n_tot, [w.n_real], precision=prec)
+        ens.sample([w.psi_cl()], w.noise_seed)
+        twa_advance(ens.h, ens.psi, 100, w.out_every, ens.new_series(100, w.out_every))
+        series = ens.new_series(w.n_steps, w.out_every)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        twa_advance(ens.h, ens.psi, w.n_steps, w.out_every, series)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = w.n_real * w.grid.cells * w.n_steps / (e0.elapsed_time(e1) * 1e-3)
+        ens.close()
+    return {"value": out["f32"], "f64_plain": out["f64_plain"], "unit": UNIT,
+            "workload": "1D Gaussian bump 256 cells x 32 streams, 1000 KDK steps, moments every 10 (launch- and moment-bound)"}
+
+
 def _uneven_rate(steps=3):
     """Uneven multi-instance batch in one handle (2D two-soliton merger: 512^2 x 128, 1024^2 x 64 and
     2048^2 x 16 streams), moments every 10 steps, the instances on parallel graph branches."""
@@ -374,6 +399,7 @@ def run_twa(args):
                                    "path": "torch.fft (cuFFT) KDK step, 32 fields, reference only"}
         cv, n, el = _oracle_rate(w)
         line["uneven_batch"] = _uneven_rate()
+        line["one_d"] = _one_d_rate()
         torch.cuda.empty_cache()
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                                 "sample": f"2 streams of the 128^3 workload, {n} KDK steps in {el:.1f} s (FP64 scipy.fft)"}
