@@ -46,10 +46,12 @@ def _headers_digest() -> str:
 
 
 def source_digest() -> str:
-    """Digest of every CUDA source and header (identifies the kernels a profile was taken on)."""
+    """Digest of the sources that define the line-pass kernels (the transform engine, the passes, their
+    instantiations): identifies the kernels a profile was taken on.  Host-side API code is left out."""
     h = hashlib.sha1()
     for f in sorted(os.listdir(CSRC)):
-        if f.endswith((".cu", ".cuh", ".h", ".inc")):
+        if f in ("fft_engine.cuh", "passes.cuh", "pipe.cuh", "passes_inst.inc", "kernels.h") or \
+                (f.startswith("passes_n") and f.endswith(".cu")):
             h.update(f.encode())
             h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]

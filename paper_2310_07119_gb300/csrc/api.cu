@@ -484,7 +484,6 @@ int closing_kick(twa_handle* h, Inst& I, float2* psi, double frac, cudaStream_t 
     return 0;
 }
 
-// Moments with a pending kick (0 for a synchronized batch); scalars into `scalars` (device).
 // Instances of a batch are independent.  With more than one, each instance's work goes to its own
 // stream between a fork on st and a join back onto st (inside a capture this makes parallel graph
 // branches), so the last wave of one instance's pass overlaps the passes of the others and an
@@ -524,6 +523,7 @@ struct Fork {
     }
 };
 
+// Moments with a pending kick (0 for a synchronized batch); scalars into `scalars` (device).
 int moments_f32(twa_handle* h, Inst& I, float2* psi, double pend, const twa_moments_out* o, double* scalars,
                 cudaStream_t st) {
     const bool v_spec = (I.mode == MODE_3D) && pend != 0.0;
@@ -978,7 +978,9 @@ int twa_advance(twa_handle* h, void* psi_work, int n_steps, int out_every, doubl
         CU(cudaStreamWaitEvent(user, h->ev_b, 0));
     }
     h->launches = 0;
-    for (auto& I : h->in) RC(closing_kick(h, I, inst_psi(I, psi_work), kh, user));
+    // the last step's closing half kick (with no step taken the batch is already synchronized)
+    if (n_out >= 1)
+        for (auto& I : h->in) RC(closing_kick(h, I, inst_psi(I, psi_work), kh, user));
     total += h->launches;
     h->launches = total;
     CU(cudaGetLastError());

@@ -1,0 +1,101 @@
+"""GPU edge cases of the C ABI: rejected arguments (with their status codes and messages), zero
+steps, a single stream (a Poisson pair with one member), the smallest transform lengths and a
+grid with three different axis lengths, each against the oracle or an exact expectation."""
+import numpy as np
+import pytest
+import torch
+
+import twa_inputs as ti
+from oracle import sp, twa
+from paper_2310_07119_gb300 import Ensemble, TwaError, twa_advance
+from paper_2310_07119_gb300 import _lib as L
+from tests.gpu_common import field_rel_l2, make_ensemble, oracle_batch
+
+pytestmark = pytest.mark.gpu
+
+F32_FIELD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("grid,n_real", [
+    (ti.Grid(3, (48, 32, 32), 1.0), [2]),        # not a power of two
+    (ti.Grid(1, (4096, 1, 1), 1.0), [2]),        # longer than the longest plan
+    (ti.Grid(2, (4, 64, 1), 1.0), [2]),          # shorter than the shortest plan
+    (ti.Grid.cube(3, 16), [0]),                   # no stream
+])
+def test_create_rejects_bad_shapes(grid, n_real):
+    with pytest.raises(TwaError) as e:
+        Ensemble([grid], ti.HBAR_3D, ti.C_UNIT, 1e-4, 1e8, n_real)
+    assert e.value.code == L.TWA_EINVAL and len(str(e.value)) > 10
+
+
+def test_create_rejects_nonpositive_physics():
+    g = ti.Grid.cube(3, 16)
+    for hb, dt, n in ((0.0, 1e-4, 1e8), (ti.HBAR_3D, -1e-4, 1e8), (ti.HBAR_3D, 1e-4, 0.0)):
+        with pytest.raises(TwaError) as e:
+            Ensemble([g], hb, ti.C_UNIT, dt, n, [2])
+        assert e.value.code == L.TWA_EINVAL
+
+
+def test_advance_rejects_steps_not_a_multiple_of_out_every():
+    w = ti.small_workload("kgauss", 3, 16, 2, 0, n_tot=1e8)
+    ens = make_ensemble([w], 0)
+    ens.sample([w.psi_cl()], w.noise_seed)
+    with pytest.raises(TwaError) as e:
+        twa_advance(ens.h, ens.psi, 15, 10, ens.new_series(10, 10))
+    assert e.value.code == L.TWA_EINVAL and "out_every" in str(e.value)
+    ens.close()
+
+
+def test_zero_steps_leave_the_batch_unchanged_and_run_reports_t0():
+    w = ti.small_workload("kgauss", 3, 16, 3, 0, n_tot=1e8)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    ens.sample([cl], w.noise_seed)
+    before = ens.fields(0).cpu().numpy().copy()
+    ens.step(0)
+    assert np.array_equal(before, ens.fields(0).cpu().numpy())
+    series = ens.run([cl], w.noise_seed, 0, 10).cpu().numpy()
+    assert series.shape[0] == 1
+    assert np.array_equal(before, ens.fields(0).cpu().numpy())     # sampled again, nothing applied
+    mo = twa.moments(twa.sample(cl, w.noise_seed, w.n_real, w.phys.n_tot, w.grid.dV), w.phys.n_tot, 1.0, 3)
+    assert abs(series[0, 0, 1] - mo["corr"]) <= 1e-2 * mo["corr"]
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_single_stream_half_pair(precision):
+    """One stream: slots (classical, stream) form one Poisson pair; with two streams the last pair
+    has one member; both against the oracle."""
+    for n_real in (1, 2):
+        w = ti.small_workload("kgauss", 3, 16, n_real, 20, n_tot=1e8)
+        cl = w.psi_cl()
+        ens = make_ensemble([w], precision)
+        ens.sample([cl], w.noise_seed)
+        ens.step(w.n_steps)
+        got = ens.fields(0).cpu().numpy().astype(np.complex128)
+        ref = oracle_batch(w, cl, w.n_steps)
+        tol = F32_FIELD_TOL if precision == 0 else 1e-10
+        assert np.all(field_rel_l2(got, ref, 3) < tol), (n_real, field_rel_l2(got, ref, 3))
+        ens.close()
+
+
+@pytest.mark.parametrize("shape", [(8,), (16,), (8, 8), (16, 8), (8, 8, 8), (64, 16, 8)])
+def test_smallest_lengths_and_unequal_axes(shape):
+    dim = len(shape)
+    g = ti.Grid(dim, tuple(list(shape[::-1]) + [1] * (3 - dim)), 1.0)
+    w = ti.Workload("kgauss" if dim > 1 else "bump1d", g, ti.Physics(ti.HBAR_3D, ti.C_UNIT, 2e-4, 1e8),
+                    3, 30, 10, 5, 777)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    ens.sample([cl], w.noise_seed)
+    ens.step(w.n_steps)
+    got = ens.fields(0).cpu().numpy().astype(np.complex128)
+    ref = oracle_batch(w, cl, w.n_steps)
+    assert np.all(field_rel_l2(got, ref, dim) < F32_FIELD_TOL), field_rel_l2(got, ref, dim)
+    ens.close()
