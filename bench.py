@@ -260,7 +260,7 @@ def _uneven_rate(steps=3):
     ws = [ti.workload_2d_merger(m, nr, 1000) for m, nr in ((512, 128), (1024, 64), (2048, 16))]
     p = ws[0].phys
     ens = Ensemble([w.grid for w in ws], p.hbar_m, p.C, p.dt, p.n_tot, [w.n_real for w in ws], want_modes=True)
-    ens.autotune(os.path.join(tempfile.gettempdir(), "twa_tune_cache.json"))
+    ens.autotune(_tune_cache_path(torch.cuda.current_device()))
     ens.sample([w.psi_cl() for w in ws], SEED)
     warm = ens.new_series(2 * OUT_EVERY, OUT_EVERY)
     twa_advance(ens.h, ens.psi, 2 * OUT_EVERY, OUT_EVERY, warm)
@@ -308,6 +308,21 @@ def _e2e(ens, w, steps=2, n_run=50):
             "call": f"twa_run({n_run} KDK steps, moments every {OUT_EVERY}) incl. sampling, per step"}
 
 
+def _max_over_ranks(ms: float, dist, device) -> float:
+    """The job's time: the slowest rank's (all_reduce MAX); the local time on one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _tune_cache_path(local_rank: int) -> str:
+    """Autotune cache of one GPU of the node (ranks tune concurrently; one file each)."""
+    return os.path.join(tempfile.gettempdir(), f"twa_tune_cache_gpu{local_rank}.json")
+
+
 def run_twa(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -326,7 +341,7 @@ def run_twa(args):
                    device=f"cuda:{local}")
     cl = w.psi_cl()
     if not args.no_tune:
-        ens.autotune(os.path.join(tempfile.gettempdir(), "twa_tune_cache.json"))
+        ens.autotune(_tune_cache_path(local))
     ens.sample([cl], w.noise_seed)
     series_w = ens.new_series(max(1, args.warmup) * OUT_EVERY, OUT_EVERY)
     twa_advance(ens.h, ens.psi, max(1, args.warmup) * OUT_EVERY, OUT_EVERY, series_w)
@@ -350,10 +365,7 @@ def run_twa(args):
     ms = e0.elapsed_time(e1)
     prof = twa_profile_read(ens.h)
     twa_profile_enable(ens.h, False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(ms, dist, "cuda")
     cell_updates = ns * w.grid.cells * OUT_EVERY * args.steps * world
     value = cell_updates / (ms * 1e-3)
     sc = series.cpu().numpy()
