@@ -228,10 +228,11 @@ int twa_sync_status(twa_handle* h, void* stream);
 /* Message of the last failure on this handle (or of the last twa_create failure if h is NULL). */
 const char* twa_last_error(const twa_handle* h);
 
-/* Autotune the FP32 pass shapes (lines per CTA) for every instance by timing candidates on
-   `stream` with scratch fields; the choice is kept in the handle and, if cache_path is not
-   NULL, merged into that JSON file (read first if it exists).  psi: a batch buffer the tuner
-   may overwrite. */
+/* Autotune the FP32 pass shapes (lines per CTA, plain or pipelined variant) for every instance,
+   the 3D pipeline (axis or plane passes) and, for several instances, whether they run on parallel
+   streams, by timing candidates on `stream` with scratch fields; the choice is kept in the handle
+   and, if cache_path is not NULL, merged into that JSON file (read first if it exists).  psi: a
+   batch buffer the tuner may overwrite. */
 int twa_autotune(twa_handle* h, void* psi, const char* cache_path, void* stream);
 
 /* Number of kernel launches the last twa_step_batch / twa_run / twa_moments call enqueued. */

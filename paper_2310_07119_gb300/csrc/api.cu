@@ -93,6 +93,8 @@ struct twa_handle {
     const void* g_psi = nullptr;
     const void* g_series = nullptr;
     int g_out_every = -1;
+    // run the instances of a multi-instance batch on parallel streams (see Fork)
+    bool fork = false;
     // pass profiler
     bool prof_on = false;
     struct ProfRec {
@@ -484,16 +486,18 @@ int closing_kick(twa_handle* h, Inst& I, float2* psi, double frac, cudaStream_t 
     return 0;
 }
 
-// Instances of a batch are independent.  With more than one, each instance's work goes to its own
+// Instances of a batch are independent.  With h->fork set, each instance's work goes to its own
 // stream between a fork on st and a join back onto st (inside a capture this makes parallel graph
-// branches), so the last wave of one instance's pass overlaps the passes of the others and an
-// uneven batch keeps the GPU full.  The pass profiler times passes one at a time and keeps st.
+// branches), so small instances that cannot fill the GPU alone overlap.  Large instances run one
+// after another: their concurrent passes compete for L1, shared memory and L2 (the 2D batch
+// 512^2 x 128 + 1024^2 x 64 + 2048^2 x 16 runs 11 % slower forked).  twa_create sets fork for
+// batches of small instances; twa_autotune times both.  The pass profiler keeps st.
 struct Fork {
     twa_handle* h;
     cudaStream_t st;
     bool on;
     int open(size_t n) {
-        on = n > 1 && !h->prof_on;
+        on = n > 1 && !h->prof_on && h->fork;
         if (!on) return 0;
         while (h->side.size() < n) {
             cudaStream_t x;
@@ -741,6 +745,9 @@ int twa_create(twa_handle** out, const twa_grid* grids, const twa_params* p, int
         if (g.dim == 3 && I.n[0] == I.n[1] && I.n[0] >= 16 && I.n[0] <= 256) I.mode = MODE_3DP;
         h->in.push_back(I);
     }
+    // fork batches whose instances are all small (at most 2^22 complex values each)
+    h->fork = n_inst > 1;
+    for (const auto& I : h->in) h->fork = h->fork && (long long)I.n_slots * I.cells <= (1LL << 22);
     int rc = 0;
     auto bail = [&](int code) {
         g_create_error = h->err;
@@ -1255,6 +1262,42 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
             }
         }
         CU(cudaMemsetAsync(I.vc, 0, (size_t)I.n_pairs * I.cells * sizeof(float2), st));
+    }
+    if (h->in.size() > 1) {
+        // multi-instance batch: time two steps of all instances forked and one after another
+        std::string key = "batch";
+        for (const auto& I : h->in)
+            key += ":" + std::to_string(I.n[0]) + "x" + std::to_string(I.n[1]) + "x" + std::to_string(I.n[2]) +
+                   "s" + std::to_string(I.n_slots);
+        auto hit = cache.find(key);
+        if (hit != cache.end()) {
+            h->fork = hit->second != 0;
+        } else {
+            float t[2] = {0.f, 0.f};
+            auto steps_all = [&](int n) -> int {
+                Fork fk{h, st, false};
+                RC(fk.open(h->in.size()));
+                for (size_t i = 0; i < h->in.size(); ++i) {
+                    cudaStream_t s;
+                    RC(fk.stream(i, &s));
+                    RC(steps_f32(h, h->in[i], inst_psi(h->in[i], psi), n, 1.0, s));
+                    RC(fk.join(i));
+                }
+                return 0;
+            };
+            for (int m = 0; m < 2; ++m) {
+                h->fork = (m == 1);
+                RC(steps_all(1));
+                CU(cudaEventRecord(e0, st));
+                RC(steps_all(2));
+                CU(cudaEventRecord(e1, st));
+                CU(cudaEventSynchronize(e1));
+                CU(cudaEventElapsedTime(&t[m], e0, e1));
+            }
+            h->fork = t[1] < 0.97f * t[0];
+            cache[key] = h->fork ? 1 : 0;
+        }
+        for (auto& I : h->in) CU(cudaMemsetAsync(I.vc, 0, (size_t)I.n_pairs * I.cells * sizeof(float2), st));
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
