@@ -99,3 +99,27 @@ def test_smallest_lengths_and_unequal_axes(shape):
     ref = oracle_batch(w, cl, w.n_steps)
     assert np.all(field_rel_l2(got, ref, dim) < F32_FIELD_TOL), field_rel_l2(got, ref, dim)
     ens.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_literal_noise_reading_samples_match_oracle(precision):
+    """noise_conv = 1 (the paper's printed variance, twice the coherent-state one) on both paths."""
+    base = ti.small_workload("kgauss", 3, 16, 4, 0, n_tot=1e6)
+    out = {}
+    for conv in (0, 1):
+        w = ti.Workload(base.name, base.grid, ti.Physics(base.phys.hbar_m, base.phys.C, base.phys.dt,
+                                                         base.phys.n_tot, conv),
+                        base.n_real, 0, base.out_every, base.psi_cl_seed, base.noise_seed)
+        cl = w.psi_cl()
+        ens = make_ensemble([w], precision)
+        ens.sample([cl], w.noise_seed)
+        got = ens.fields(0).cpu().numpy().astype(np.complex128)
+        ref = twa.sample(cl, w.noise_seed, w.n_real, w.phys.n_tot, w.grid.dV, conv)
+        tol = 2 * np.finfo(np.float32).eps if precision == 0 else 1e-14
+        assert np.max(np.abs(got - ref)) <= tol * np.abs(ref).max()
+        out[conv] = got[1:] - cl
+        amp = np.abs(cl).max()
+        ens.close()
+    # same normals, sigma scaled by sqrt(2) (up to the rounding of the stored fields)
+    atol = 4 * np.finfo(np.float32).eps * amp if precision == 0 else 1e-13 * amp
+    assert np.max(np.abs(out[1] - np.sqrt(2.0) * out[0])) <= atol
