@@ -114,6 +114,49 @@ def run(psi_cl: np.ndarray, hbar: float, C: float, dt: float, L: float, dim: int
     return np.array(times), series, batch
 
 
+def adaptive_dt(batch: np.ndarray, hbar: float, C: float, L: float, dim: int, c_f: float) -> float:
+    """Time step of Sec. III.B.2 (the dynamic Delta t rule), read in normalized units:
+
+        Delta t = 2 pi c_f min[ hbar / max|V| ,  L dx / (pi hbar) ]
+
+    The first bound keeps the potential phase V Delta t / hbar of every stream and cell below
+    2 pi c_f; the second keeps the gradient of the kinetic phase from aliasing (the footnote's
+    dt < 4 pi / (hbar k_max dk) with k_max = pi / dx, dk = 2 pi / L equals it for c_f = 1/pi; the
+    printed m L / (M pi hbar) lacks one factor of L, equal to it for L = 1).  dx is the smallest
+    cell side; max|V| runs over every stream and cell of the batch.
+    """
+    shape = batch.shape[-dim:]
+    dx = min(L / n for n in shape)
+    kin = L * dx / (math.pi * hbar)
+    vmax = max(float(np.max(np.abs(sp.potential(b, C, L, dim)))) for b in batch)
+    pot = hbar / vmax if vmax > 0 else math.inf
+    return 2.0 * math.pi * c_f * min(pot, kin)
+
+
+def run_adaptive(psi_cl: np.ndarray, hbar: float, C: float, L: float, dim: int, n_tot: float,
+                 n_real: int, seed: int, n_out: int, out_every: int, c_f: float,
+                 noise_conv: int = 0, with_modes: bool = True, batch: np.ndarray = None):
+    """Like ``run`` with the dynamic time step: before each output interval of ``out_every`` KDK
+    steps, Delta t is set by ``adaptive_dt`` from the batch at the interval's start and kept for
+    the interval.  Returns (times, list of moment dicts, final batch, list of the Delta t used).
+    """
+    M = psi_cl.size
+    dV = (L ** dim) / M
+    if batch is None:
+        batch = sample(psi_cl, seed, n_real, n_tot, dV, noise_conv)
+    t = 0.0
+    times, series, dts = [0.0], [moments(batch, n_tot, L, dim, with_modes)], []
+    for _ in range(n_out):
+        dt = adaptive_dt(batch, hbar, C, L, dim, c_f)
+        for _ in range(out_every):
+            batch = sp.step(batch, hbar, C, dt, L, dim)
+        t += out_every * dt
+        dts.append(dt)
+        times.append(t)
+        series.append(moments(batch, n_tot, L, dim, with_modes))
+    return np.array(times), series, batch, dts
+
+
 def q_physical(Q_sim: float, n_sim: float, n_phys: float) -> float:
     """Q_p = (n_s / n_p) Q_s (Eq. Q_relation), valid while Q << 1."""
     return Q_sim * n_sim / n_phys

@@ -158,3 +158,51 @@ def test_early_growth_of_Q_is_quadratic(seed):
     t, series, _ = twa.run(psi, 0.05, 4 * np.pi, 2e-3, 1.0, 1, 1e8, 400, seed, 60, 6, with_modes=False)
     q = np.array([s["Q"] for s in series])
     assert 1.7 < twa.stable_growth_exponent(t, q) < 2.3
+
+
+def _cosine_field(M, n, eps, L=1.0):
+    x = np.arange(M) * L / M
+    return np.sqrt(1.0 + eps * np.cos(2 * np.pi * n * x / L)).astype(np.complex128)
+
+
+def test_adaptive_dt_potential_bound_matches_the_cosine_closed_form():
+    # rho = 1 + eps cos(k x)  ->  V = -C eps cos(k x) / k^2,  max|V| = C eps / k^2
+    M, n, eps, C, hb, c_f = 64, 2, 0.3, 4 * np.pi, 1e-3, 0.1
+    psi = _cosine_field(M, n, eps)
+    k = 2 * np.pi * n
+    expect_pot = 2 * np.pi * c_f * hb * k * k / (C * eps)
+    kin = 2 * np.pi * c_f * (1.0 / M) / (np.pi * hb)
+    assert expect_pot < kin
+    got = twa.adaptive_dt(psi[None], hb, C, 1.0, 1, c_f)
+    assert got == pytest.approx(expect_pot, rel=1e-12)
+
+
+def test_adaptive_dt_kinetic_bound_is_the_gradient_aliasing_rule():
+    # C = 0: only the kinetic bound; for c_f = 1/pi it is the footnote's 4 pi / (hbar k_max dk)
+    hb, L = 0.0122, 2.0
+    for shape in ((64,), (32, 64), (16, 32, 128)):
+        psi = np.ones(shape, dtype=np.complex128)
+        dx = min(L / m for m in shape)
+        kmax, dk = np.pi / dx, 2 * np.pi / L
+        got = twa.adaptive_dt(psi[None], hb, 0.0, L, len(shape), 1.0 / np.pi)
+        assert got == pytest.approx(4 * np.pi / (hb * kmax * dk), rel=1e-12)
+
+
+def test_adaptive_run_without_gravity_is_the_fixed_step_run():
+    M, hb = 64, 1e-2
+    psi = _cosine_field(M, 3, 0.2)
+    psi /= np.sqrt(np.sum(np.abs(psi) ** 2) / M)
+    dt = twa.adaptive_dt(psi[None], hb, 0.0, 1.0, 1, 0.05)
+    ta, sa, ba, dts = twa.run_adaptive(psi, hb, 0.0, 1.0, 1, 1e4, 3, 11, 4, 5, 0.05)
+    tf, sf, bf = twa.run(psi, hb, 0.0, dt, 1.0, 1, 1e4, 3, 11, 20, 5)
+    assert dts == [dt] * 4
+    assert np.allclose(ta, tf, rtol=0, atol=1e-15) and np.array_equal(ba, bf)
+
+
+def test_adaptive_dt_shrinks_while_an_overdensity_collapses():
+    M, hb, C = 128, 2e-3, 4 * np.pi
+    x = np.arange(M) / M
+    psi = np.sqrt(1 + 2.0 * np.exp(-(x - 0.5) ** 2 / (2 * 0.05 ** 2))).astype(np.complex128)
+    psi /= np.sqrt(np.sum(np.abs(psi) ** 2) / M)
+    _, _, _, dts = twa.run_adaptive(psi, hb, C, 1.0, 1, 1e6, 2, 5, 6, 20, 0.02)
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(dts, dts[1:])) and dts[-1] < 0.9 * dts[0]
