@@ -146,6 +146,23 @@ int twa_moments(twa_handle* h, int inst, const void* psi, const twa_moments_out*
    profiler is on).  n_steps must be a multiple of out_every. */
 int twa_advance(twa_handle* h, void* psi, int n_steps, int out_every, double* series, void* stream);
 
+/* Continue a synchronized FP32 batch by n_out output intervals of out_every KDK steps with the
+   dynamic time step of Sec. III.B.2 (the Delta t rule), chosen before each interval from the
+   batch at its start and kept for the interval:
+       dt = 2 pi c_f min[ hbar_m / max|V| ,  L dx / (pi hbar_m) ]
+   with max|V| over every stream and cell of an instance, dx its smallest cell side, and the
+   minimum taken over instances (all instances share the time axis).  The second bound keeps the
+   gradient of the kinetic phase from aliasing (the printed term lacks one factor of L; for
+   c_f = 1/pi it is the footnote's dt < 4 pi / (hbar k_max dk)); c_f > 0 is the caller's safety
+   factor (the paper does not state its value).  Merged half kicks carry the step change.
+   series: as for twa_advance (n_out + 1 outputs, device FP64); times: HOST array of n_out + 1
+   doubles receiving the time of each output (times[0] = 0).  Reads max|V| back before every
+   interval, so the call synchronizes `stream` n_out times and is not graph-captured; the handle's
+   own dt and phase tables are restored before it returns.  FP32 path only (TWA_EINVAL
+   otherwise); TWA_ENONFINITE if the potential is not finite. */
+int twa_advance_adaptive(twa_handle* h, void* psi, int n_out, int out_every, double c_f, double* series,
+                         double* times, void* stream);
+
 /* Full run (Sec. III.B): twa_sample(psi_cl, seed) into psi_work, then twa_advance. */
 int twa_run(twa_handle* h, const void* psi_cl, uint64_t seed, int n_steps, int out_every,
             void* psi_work, double* series, void* stream);

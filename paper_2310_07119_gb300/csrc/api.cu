@@ -76,6 +76,7 @@ struct twa_handle {
     std::vector<Inst> in;
     std::string err;
     int* d_err = nullptr;
+    unsigned* d_vmax = nullptr;  // [n_inst] largest |W| per instance (float bits), adaptive steps
     int* d_counter = nullptr;
     double* d_cur = nullptr;  // [n_inst][TWA_NSCALARS] scalars of the current output
     std::map<int, float4*> tw32;
@@ -755,6 +756,7 @@ int twa_create(twa_handle** out, const twa_grid* grids, const twa_params* p, int
         return code;
     };
     if ((rc = dalloc(h, &h->d_err, 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_vmax, (size_t)n_inst))) return bail(rc);
     if ((rc = dalloc(h, &h->d_counter, 1))) return bail(rc);
     if ((rc = dalloc(h, &h->d_cur, (size_t)n_inst * TWA_NSCALARS))) return bail(rc);
     cudaMemset(h->d_err, 0, sizeof(int));
@@ -903,6 +905,73 @@ int run_interval_f32(twa_handle* h, void* psi, int out_every, double a_first, do
     return 0;
 }
 
+// Rewrite the FP32 kinetic-phase tables of every axis for the handle's current dt (as build_tables:
+// phase reduced in FP64, stored as float hi + lo), in stream order.
+int write_phase_tables(twa_handle* h, Inst& I, cudaStream_t st) {
+    const double hb = h->p.hbar_m, dt = h->p.dt;
+    for (int a = 0; a < 3; ++a) {
+        const int n = I.n[a];
+        std::vector<float4> phc(n);
+        for (int j = 0; j < n; ++j) {
+            const double k = (a < I.dim) ? wavenumber(j, n, I.L) : 0.0;
+            double c, s;
+            phase_of(hb * k * k * dt / 2.0, c, s);
+            const float cx = (float)(c / n), sy = (float)(s / n);
+            phc[j] = make_float4(cx, sy, (float)(c / n - (double)cx), (float)(s / n - (double)sy));
+        }
+        CU(cudaMemcpyAsync(I.ph[a], phc.data(), (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, st));
+    }
+    return 0;
+}
+
+// Set the time step of every later kick and drift (a captured interval graph is dropped).
+int set_dt(twa_handle* h, double dt, cudaStream_t st) {
+    h->p.dt = dt;
+    for (auto& I : h->in) RC(write_phase_tables(h, I, st));
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return 0;
+}
+
+// Time step of Sec. III.B.2 from the synchronized (kick pending) FP32 batch: per instance the
+// largest |V| = |C| max|W| / cells over its streams and cells (W, the packed Poisson field, made
+// real along x first where it is kept x-spectral), then
+//   dt = 2 pi c_f min over instances of min[ hbar / max|V| ,  L dx_min / (pi hbar) ].
+// Reads the maxima back: synchronizes the stream.
+int adaptive_dt(twa_handle* h, void* psi, double c_f, cudaStream_t st, double* dt_out) {
+    const size_t ni = h->in.size();
+    CU(cudaMemsetAsync(h->d_vmax, 0, ni * sizeof(unsigned), st));
+    for (size_t i = 0; i < ni; ++i) {
+        Inst& I = h->in[i];
+        float2* f = inst_psi(I, psi);
+        const bool v_spec = I.mode == MODE_3D;
+        if (v_spec) RC(run_pass(h, I, f, 0, OP_INV, 0.0, I.vc, nullptr, I.n_pairs, st));
+        launch_max_abs(I.vc, (long long)I.n_pairs * I.cells, h->d_vmax + i, st);
+        ++h->launches;
+        if (v_spec) RC(run_pass(h, I, f, 0, OP_FWD, 0.0, I.vc, nullptr, I.n_pairs, st, 0, 0, 1.0f / (float)I.n[0]));
+    }
+    std::vector<unsigned> bits(ni);
+    CU(cudaMemcpyAsync(bits.data(), h->d_vmax, ni * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double dt = INFINITY;
+    const double hb = h->p.hbar_m;
+    for (size_t i = 0; i < ni; ++i) {
+        const Inst& I = h->in[i];
+        float w;
+        std::memcpy(&w, &bits[i], sizeof(float));
+        const double vmax = std::fabs(h->p.C) * (double)w / (double)I.cells;
+        double dx = INFINITY;
+        for (int a = 0; a < I.dim; ++a) dx = std::min(dx, I.L / I.n[a]);
+        const double kin = I.L * dx / (M_PI * hb);
+        const double pot = vmax > 0.0 ? hb / vmax : INFINITY;
+        dt = std::min(dt, std::min(pot, kin));
+    }
+    *dt_out = 2.0 * M_PI * c_f * dt;
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -990,6 +1059,58 @@ int twa_advance(twa_handle* h, void* psi_work, int n_steps, int out_every, doubl
         for (auto& I : h->in) RC(closing_kick(h, I, inst_psi(I, psi_work), kh, user));
     total += h->launches;
     h->launches = total;
+    CU(cudaGetLastError());
+    return TWA_OK;
+}
+
+int twa_advance_adaptive(twa_handle* h, void* psi_work, int n_out, int out_every, double c_f, double* series,
+                         double* times, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!psi_work || !series || !times || n_out < 0 || out_every <= 0 || !(c_f > 0.0))
+        return fail(h, TWA_EINVAL, "twa_advance_adaptive: bad argument (need n_out >= 0, out_every > 0, c_f > 0)");
+    if (h->p.precision != TWA_F32) return fail(h, TWA_EINVAL, "twa_advance_adaptive: FP32 path only");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double dt0 = h->p.dt;
+    long long total = 0;
+    h->launches = 0;
+    CU(cudaMemsetAsync(h->d_counter, 0, sizeof(int), st));
+    for (size_t i = 0; i < h->in.size(); ++i) {
+        Inst& I = h->in[i];
+        float2* f = inst_psi(I, psi_work);
+        RC(poisson_init(h, I, f, st));
+        RC(moments_f32(h, I, f, 0.0, nullptr, h->d_cur + i * TWA_NSCALARS, st));
+    }
+    launch_store_series(h->d_cur, series, h->d_counter, (int)h->in.size() * TWA_NSCALARS, st);
+    ++h->launches;
+    times[0] = 0.0;
+    double t = 0.0, dt_prev = 0.0;
+    int rc = 0;
+    for (int o = 1; o <= n_out && rc == 0; ++o) {
+        double dt = 0.0;
+        if ((rc = adaptive_dt(h, psi_work, c_f, st, &dt))) break;
+        if (!(dt > 0.0) || !std::isfinite(dt)) {
+            rc = fail(h, TWA_ENONFINITE, "twa_advance_adaptive: no finite time step (non-finite potential)");
+            break;
+        }
+        if ((rc = set_dt(h, dt, st))) break;
+        // the pending closing half kick of the previous interval (dt_prev / 2) merges with this
+        // interval's opening half kick (dt / 2)
+        const double a_first = (o == 1) ? 0.5 : 0.5 + 0.5 * dt_prev / dt;
+        total += h->launches;
+        h->launches = 0;
+        if ((rc = run_interval_f32(h, psi_work, out_every, a_first, series, st))) break;
+        t += out_every * dt;
+        times[o] = t;
+        dt_prev = dt;
+    }
+    if (rc == 0 && n_out >= 1)
+        for (auto& I : h->in)
+            if ((rc = closing_kick(h, I, inst_psi(I, psi_work), 0.5, st))) break;
+    total += h->launches;
+    const int rc2 = set_dt(h, dt0, st);
+    h->launches = total;
+    if (rc) return rc;
+    if (rc2) return rc2;
     CU(cudaGetLastError());
     return TWA_OK;
 }

@@ -23,6 +23,9 @@ int launch_moments_modes(const float2* spec, long long cells, int n_slots, doubl
 int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, int nb_m, double dV,
                           double q_offset, double* scalars, int* err_word, cudaStream_t st);
 int launch_store_series(const double* cur, double* series, int* counter, int n, cudaStream_t st);
+// max over the batch of |re| and |im| of n complex values, folded into *vmax (float bits; *vmax must
+// start at 0 or at an earlier maximum)
+int launch_max_abs(const float2* buf, long long n, unsigned* vmax, cudaStream_t st);
 
 // Plain FP64 comparator path (one realization per launch, no fusion).
 struct Geom64 {

@@ -213,6 +213,26 @@ __global__ void k_moments_modes(const float2* __restrict__ spec, long long cells
     block_reduce_store<NP_MODES>(v, part);
 }
 
+// Largest |re| or |im| over n complex values (the packed potentials of a batch), folded into *vmax
+// as float bits: for non-negative floats the unsigned order of the bits is their numeric order.
+// Non-finite values are skipped (the moments flag them).
+__global__ void k_max_abs(const float2* __restrict__ buf, long long n, unsigned* vmax) {
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = __ldcg(&buf[i]);
+        const float a = fmaxf(fabsf(v.x), fabsf(v.y));
+        if (a <= 3.0e38f) m = fmaxf(m, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+        atomicMax(vmax, __float_as_uint(m));
+    }
+}
+
 // Sum the per-block partials in block order and form the TWA_NSCALARS scalars of one instance.
 __global__ void k_finish_scalars(const double* __restrict__ part_r, int nb_r, const double* __restrict__ part_m,
                                  int nb_m, double dV, double q_offset, double* scalars, int* err_word) {
@@ -297,6 +317,11 @@ int launch_moments_modes(const float2* spec, long long cells, int n_slots, doubl
 int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, int nb_m, double dV,
                           double q_offset, double* scalars, int* err_word, cudaStream_t st) {
     k_finish_scalars<<<1, 256, 0, st>>>(part_r, nb_r, part_m, nb_m, dV, q_offset, scalars, err_word);
+    return 0;
+}
+int launch_max_abs(const float2* buf, long long n, unsigned* vmax, cudaStream_t st) {
+    const long long b = (n + 255) / 256;
+    k_max_abs<<<(int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8), 256, 0, st>>>(buf, n, vmax);
     return 0;
 }
 int launch_store_series(const double* cur, double* series, int* counter, int n, cudaStream_t st) {

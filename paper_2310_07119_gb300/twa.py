@@ -17,7 +17,7 @@ from . import _lib as L
 __all__ = [
     "TwaError", "twa_create", "twa_destroy", "twa_batch_elems", "twa_sample", "twa_step_batch",
     "twa_moments", "twa_run", "twa_sync_status", "twa_last_error", "twa_autotune",
-    "twa_last_launch_count", "twa_advance", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
+    "twa_last_launch_count", "twa_advance", "twa_advance_adaptive", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
     "F64_PLAIN", "SCALAR_NAMES", "PASS_NAMES",
 ]
 
@@ -112,6 +112,15 @@ def twa_run(h, psi_cl, seed: int, n_steps: int, out_every: int, psi_work, series
 
 def twa_advance(h, psi, n_steps: int, out_every: int, series, stream=None) -> None:
     _check(_lib().twa_advance(h, _ptr(psi), int(n_steps), int(out_every), _ptr(series), _stream(stream)), h)
+
+
+def twa_advance_adaptive(h, psi, n_out: int, out_every: int, c_f: float, series, stream=None):
+    """Adaptive-step continuation (see include/twa.h); returns the output times (numpy, n_out + 1)."""
+    import numpy as np
+    times = (ctypes.c_double * (int(n_out) + 1))()
+    _check(_lib().twa_advance_adaptive(h, _ptr(psi), int(n_out), int(out_every), float(c_f), _ptr(series), times,
+                                       _stream(stream)), h)
+    return np.array(times[:], dtype=np.float64)
 
 
 def twa_profile_enable(h, on: bool) -> None:
