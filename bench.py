@@ -225,6 +225,27 @@ def _cufft_reference_rate(w, batch=32, steps=5):
     return batch * m ** 3 * steps / (e0.elapsed_time(e1) * 1e-3)
 
 
+def _adaptive_rate(ens, w, n_out=3, c_f=0.01):
+    """The bench batch advanced with the dynamic time step of Sec. III.B.2 (twa_advance_adaptive):
+    the step is chosen before every output interval, which reads max|V| back (one host
+    synchronization per interval) and runs the interval without graph replay."""
+    import torch
+    from paper_2310_07119_gb300 import twa_advance_adaptive
+    ens.sample([w.psi_cl()], w.noise_seed)
+    twa_advance_adaptive(ens.h, ens.psi, 1, OUT_EVERY, c_f, ens.new_series(OUT_EVERY, OUT_EVERY))
+    series = ens.new_series(n_out * OUT_EVERY, OUT_EVERY)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    times = twa_advance_adaptive(ens.h, ens.psi, n_out, OUT_EVERY, c_f, series)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    steps = (times[1:] - times[:-1]) / OUT_EVERY
+    return {"value": STREAMS * w.grid.cells * OUT_EVERY * n_out / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / n_out, "c_f": c_f, "dt_first": float(steps[0]), "dt_last": float(steps[-1])}
+
+
 def _one_d_rate():
     """The 1D workload (256 cells, 32 streams + classical, 1000 KDK steps, moments every 10): one
     on-chip launch per output interval on the FP32 path; the FP64 plain path on the same run."""
@@ -404,6 +425,7 @@ def run_twa(args):
     }
     if rank == 0 and not args.no_extras and ns == STREAMS:
         line["e2e"] = _e2e(ens, w)
+        line["adaptive"] = _adaptive_rate(ens, w)
         ens.close()
         torch.cuda.empty_cache()
         line["f64_plain"] = {"value": _f64_plain_rate(w), "unit": UNIT, "path": "TWA_F64_PLAIN, 1 stream + classical, 128^3"}
