@@ -114,6 +114,34 @@ def run(psi_cl: np.ndarray, hbar: float, C: float, dt: float, L: float, dim: int
     return np.array(times), series, batch
 
 
+def phase_moments(batch: np.ndarray, n_tot: float, L: float, dim: int) -> dict:
+    """Mass-weighted amplitude and phase variances of the ensemble (Eq. varA, Eq. varPhi).
+
+    Per cell, over slots 1..N_s: A_s = |psi_s|, <A> its mean and <dA^2> its (population)
+    variance; dphi_s = arg(psi_s conj(mean psi)) in (-pi, pi], the phase of each stream relative
+    to the ensemble-mean field (0 reference where the mean field vanishes), and <dphi^2> its mean
+    square.  With <rho> the Weyl-corrected mean density of ``moments``:
+        Var(A~)   = sum_g dV <rho> <dA^2> / <A>
+        Var(phi~) = sum_g dV <rho> <dphi^2> / (pi^2 / 3)
+    The printed normalization of the phase variance is pi / sqrt(3), the standard deviation of a
+    uniformly distributed phase; it is read as the variance pi^2 / 3, so that a fully random phase
+    gives the total mass.
+    """
+    s = batch[1:]
+    dV = (L ** dim) / batch[0].size
+    A = np.abs(s)
+    a_mean = A.mean(0)
+    a_var = (A ** 2).mean(0) - a_mean ** 2
+    mean_psi = s.mean(0)
+    dphi = np.angle(s * np.conj(mean_psi))
+    phi2 = (dphi ** 2).mean(0)
+    rho = (np.abs(s) ** 2).mean(0) - 1.0 / (2.0 * n_tot * dV)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        wa = np.where(a_mean > 0, rho * a_var / a_mean, 0.0)
+    return {"var_a_cell": a_var, "a_mean": a_mean, "phi2_cell": phi2,
+            "var_a": float(np.sum(wa) * dV), "var_phi": float(np.sum(rho * phi2) * dV / (math.pi ** 2 / 3.0))}
+
+
 def adaptive_dt(batch: np.ndarray, hbar: float, C: float, L: float, dim: int, c_f: float) -> float:
     """Time step of Sec. III.B.2 (the dynamic Delta t rule), read in normalized units:
 

@@ -206,3 +206,50 @@ def test_adaptive_dt_shrinks_while_an_overdensity_collapses():
     psi /= np.sqrt(np.sum(np.abs(psi) ** 2) / M)
     _, _, _, dts = twa.run_adaptive(psi, hb, C, 1.0, 1, 1e6, 2, 5, 6, 20, 0.02)
     assert all(b <= a * (1 + 1e-12) for a, b in zip(dts, dts[1:])) and dts[-1] < 0.9 * dts[0]
+
+
+def _weyl(n_tot, dV):
+    return 1.0 / (2.0 * n_tot * dV)
+
+
+def test_phase_variance_of_rotated_copies_is_the_variance_of_the_angles():
+    # streams psi0 e^{i theta_s}: amplitudes equal (Var A = 0), dphi_s = theta_s - mean angle
+    M, n_tot = 32, 1e6
+    rng = np.random.default_rng(3)
+    psi0 = (1.0 + 0.5 * rng.random(M)) * np.exp(1j * rng.uniform(0, 2 * np.pi, M))
+    theta = np.array([-0.3, -0.1, 0.05, 0.15, 0.2])
+    theta -= theta.mean()
+    batch = np.concatenate([psi0[None], psi0[None] * np.exp(1j * theta)[:, None]])
+    pm = twa.phase_moments(batch, n_tot, 1.0, 1)
+    dV = 1.0 / M
+    rho = np.abs(psi0) ** 2 - _weyl(n_tot, dV)
+    assert pm["var_a"] == pytest.approx(0.0, abs=1e-12)
+    # the mean field psi0 mean(e^{i theta}) sits at the phase of psi0 plus arg mean(e^{i theta})
+    ref_phase = np.angle(np.mean(np.exp(1j * theta)))
+    expect = np.sum(rho * np.mean((theta - ref_phase) ** 2)) * dV / (np.pi ** 2 / 3)
+    assert pm["var_phi"] == pytest.approx(expect, rel=1e-12)
+
+
+def test_amplitude_variance_of_scaled_copies():
+    # streams c_s psi0 with real c_s > 0: phases equal, Var A = Var(c) |psi0|^2, <A> = mean(c) |psi0|
+    M, n_tot = 16, 1e5
+    psi0 = np.exp(1j * np.linspace(0, 1, M)) * (1 + np.arange(M) / M)
+    c = np.array([0.8, 1.0, 1.1, 1.3])
+    batch = np.concatenate([psi0[None], c[:, None] * psi0[None]])
+    pm = twa.phase_moments(batch, n_tot, 2.0, 1)
+    dV = 2.0 / M
+    a2 = np.abs(psi0) ** 2
+    rho = np.mean(c ** 2) * a2 - _weyl(n_tot, dV)
+    expect = np.sum(rho * np.var(c) * a2 / (np.mean(c) * np.abs(psi0))) * dV
+    assert pm["var_a"] == pytest.approx(expect, rel=1e-12)
+    assert pm["var_phi"] == pytest.approx(0.0, abs=1e-20)
+
+
+def test_fully_random_phase_gives_about_the_mass():
+    # equally spaced phases about a vanishing mean field: <dphi^2> -> pi^2/3 (1 + 2/N^2)
+    N, M, n_tot = 64, 8, 1e9
+    phases = 2 * np.pi * (np.arange(N) + 0.5) / N - np.pi
+    batch = np.concatenate([np.ones((1, M)), np.exp(1j * phases)[:, None] * np.ones((1, M))]).astype(np.complex128)
+    pm = twa.phase_moments(batch, n_tot, 1.0, 1)
+    mass = np.sum(np.mean(np.abs(batch[1:]) ** 2, 0) - _weyl(n_tot, 1.0 / M)) / M
+    assert pm["var_phi"] == pytest.approx(mass, rel=2e-3)
