@@ -246,6 +246,24 @@ def _adaptive_rate(ens, w, n_out=3, c_f=0.01):
             "ms_per_step": ms / n_out, "c_f": c_f, "dt_first": float(steps[0]), "dt_last": float(steps[-1])}
 
 
+def _phase_moments_cost(ens, w, reps=3):
+    """Amplitude and phase variances (Eq. varA, Eq. varPhi) of the bench batch: two reads of every
+    stream per call (means, then deviations and phases)."""
+    import torch
+    from paper_2310_07119_gb300 import twa_phase_moments
+    tot = twa_phase_moments(ens.h, 0, ens.psi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        twa_phase_moments(ens.h, 0, ens.psi, totals=tot)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = 2 * STREAMS * w.grid.cells * 8
+    return {"ms_per_call": ms, "GBps": nbytes / (ms * 1e-3) / 1e9, "var_a": float(tot[0]), "var_phi": float(tot[1])}
+
+
 def _one_d_rate():
     """The 1D workload (256 cells, 32 streams + classical, 1000 KDK steps, moments every 10): one
     on-chip launch per output interval on the FP32 path; the FP64 plain path on the same run."""
@@ -426,6 +444,7 @@ def run_twa(args):
     if rank == 0 and not args.no_extras and ns == STREAMS:
         line["e2e"] = _e2e(ens, w)
         line["adaptive"] = _adaptive_rate(ens, w)
+        line["phase_moments"] = _phase_moments_cost(ens, w)
         ens.close()
         torch.cuda.empty_cache()
         line["f64_plain"] = {"value": _f64_plain_rate(w), "unit": UNIT, "path": "TWA_F64_PLAIN, 1 stream + classical, 128^3"}

@@ -163,6 +163,18 @@ int twa_advance(twa_handle* h, void* psi, int n_steps, int out_every, double* se
 int twa_advance_adaptive(twa_handle* h, void* psi, int n_out, int out_every, double c_f, double* series,
                          double* times, void* stream);
 
+/* Amplitude and phase variances of instance `inst` of a synchronized batch (Eq. varA, Eq. varPhi):
+   per cell over the streams, A_s = |psi_s| with mean <A> and variance <dA^2>, and dphi_s =
+   arg(psi_s conj(<psi>)) in (-pi, pi] (the phase relative to the ensemble-mean field; reference 0
+   where that vanishes) with mean square <dphi^2>; with <rho> the Weyl-corrected mean density,
+       totals[0] = sum_g dV <rho> <dA^2> / <A>,   totals[1] = sum_g dV <rho> <dphi^2> / (pi^2 / 3)
+   (the printed pi / sqrt(3) read as the variance of a uniform phase, so a fully random phase gives
+   the total mass).  var_a[cells], phi2[cells]: optional per-cell <dA^2> and <dphi^2>.  All outputs
+   device FP64; sums in double-float (FP32 path) or FP64, fixed order.  Uses the instance's moment
+   scratch: do not overlap with twa_moments of the same instance on another stream. */
+int twa_phase_moments(twa_handle* h, int inst, const void* psi, double* var_a, double* phi2, double* totals,
+                      void* stream);
+
 /* Full run (Sec. III.B): twa_sample(psi_cl, seed) into psi_work, then twa_advance. */
 int twa_run(twa_handle* h, const void* psi_cl, uint64_t seed, int n_steps, int out_every,
             void* psi_work, double* series, void* stream);

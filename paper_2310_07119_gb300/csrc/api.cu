@@ -1063,6 +1063,25 @@ int twa_advance(twa_handle* h, void* psi_work, int n_steps, int out_every, doubl
     return TWA_OK;
 }
 
+int twa_phase_moments(twa_handle* h, int inst, const void* psi, double* var_a, double* phi2, double* totals,
+                      void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!psi || !totals || inst < 0 || inst >= (int)h->in.size())
+        return fail(h, TWA_EINVAL, "twa_phase_moments: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    Inst& I = h->in[inst];
+    const double weyl = 1.0 / (2.0 * h->p.n_tot * I.dV);
+    if (h->p.precision == TWA_F32)
+        launch_phase_moments(inst_psi(I, const_cast<void*>(psi)), I.cells, I.n_slots, weyl, I.dV, var_a, phi2, I.part_r,
+                             totals, st);
+    else
+        launch_phase_moments_f64(static_cast<const double2*>(psi) + I.off, I.cells, I.n_slots, weyl, I.dV, var_a, phi2,
+                                 I.part_r, totals, st);
+    h->launches = 2;
+    CU(cudaGetLastError());
+    return TWA_OK;
+}
+
 int twa_advance_adaptive(twa_handle* h, void* psi_work, int n_out, int out_every, double c_f, double* series,
                          double* times, void* stream) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");

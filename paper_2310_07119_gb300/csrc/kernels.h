@@ -26,6 +26,11 @@ int launch_store_series(const double* cur, double* series, int* counter, int n, 
 // max over the batch of |re| and |im| of n complex values, folded into *vmax (float bits; *vmax must
 // start at 0 or at an earlier maximum)
 int launch_max_abs(const float2* buf, long long n, unsigned* vmax, cudaStream_t st);
+// amplitude and phase variances of one synchronized instance; part: moments_blocks(cells) * 2 doubles
+int launch_phase_moments(const float2* psi, long long cells, int n_slots, double weyl, double dV, double* var_a,
+                         double* phi2, double* part, double* out, cudaStream_t st);
+int launch_phase_moments_f64(const double2* psi, long long cells, int n_slots, double weyl, double dV,
+                             double* var_a, double* phi2, double* part, double* out, cudaStream_t st);
 
 // Plain FP64 comparator path (one realization per launch, no fusion).
 struct Geom64 {

@@ -101,6 +101,84 @@ struct DF {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// FP64 counterpart of DF for the plain FP64 path.
+struct DAcc {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double a) { v += a; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <class T2> struct AccOf;
+template <> struct AccOf<float2> { using type = DF; using real = float; };
+template <> struct AccOf<double2> { using type = DAcc; using real = double; };
+
+// Amplitude and phase moments (Eq. varA, Eq. varPhi) of a synchronized instance, one thread per
+// cell, two passes over the streams (slots 1..n): the first sums psi, |psi| and |psi|^2, the
+// second the squared deviations (A_s - <A>)^2 and dphi_s^2, dphi_s = arg(psi_s conj(<psi>)) (0
+// reference where the mean field vanishes).  Per block: sum of <rho> Var(A) / <A> and of
+// <rho> <dphi^2>, <rho> the Weyl-corrected mean density.
+template <class T2>
+__global__ void k_phase_moments(const T2* __restrict__ psi, long long cells, int n_slots, double weyl,
+                                double* var_a, double* phi2, double* part) {
+    using Acc = typename AccOf<T2>::type;
+    using R = typename AccOf<T2>::real;
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (g < cells) {
+        const int ns = n_slots - 1;
+        Acc sa, sa2, sx, sy;
+        for (int s = 1; s < n_slots; ++s) {
+            const T2 z = psi[(long long)s * cells + g];
+            const R a2 = z.x * z.x + z.y * z.y;
+            sa.add(sqrt(a2));
+            sa2.add(a2);
+            sx.add(z.x);
+            sy.add(z.y);
+        }
+        const double am = sa.value() / ns, mx = sx.value() / ns, my = sy.value() / ns;
+        const double mm = sqrt(mx * mx + my * my);
+        const R ux = (R)(mm > 0.0 ? mx / mm : 1.0), uy = (R)(mm > 0.0 ? my / mm : 0.0);
+        Acc da, dp;
+        for (int s = 1; s < n_slots; ++s) {
+            const T2 z = psi[(long long)s * cells + g];
+            const R d = sqrt(z.x * z.x + z.y * z.y) - (R)am;
+            da.add(d * d);
+            const R ph = atan2(z.y * ux - z.x * uy, z.x * ux + z.y * uy);  // arg(z conj(u))
+            dp.add(ph * ph);
+        }
+        const double va = da.value() / ns, p2 = dp.value() / ns;
+        const double rho = sa2.value() / ns - weyl;
+        if (var_a) var_a[g] = va;
+        if (phi2) phi2[g] = p2;
+        v[0] = am > 0.0 ? rho * va / am : 0.0;
+        v[1] = rho * p2;
+    }
+    block_reduce_store<2>(v, part);
+}
+
+// Sum the block partials in block order: out = {sum dV part_0, sum dV part_1 / (pi^2 / 3)}.
+__global__ void k_finish_phase(const double* __restrict__ part, int nb, double dV, double* out) {
+    __shared__ double red[2][256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 256) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = red[0][0] * dV;
+        out[1] = red[1][0] * dV / (3.14159265358979323846 * 3.14159265358979323846 / 3.0);
+    }
+}
+
 // Position-space moments (Eq. E[op], Eq. Q) of one instance, one thread per cell, streams summed
 // in slot order (each |psi|^2 is formed in FP32, exact to its rounding, and summed in double-float).
 // The pending half kick (kick != 0) is applied on the fly to the mean field; |psi|^2 does not
@@ -313,6 +391,22 @@ int launch_moments_modes(const float2* spec, long long cells, int n_slots, doubl
     k_moments_modes<<<moments_blocks(cells), 256, 0, st>>>(spec, cells, n_slots, anorm2, inv_ns, nk_mean,
                                                            nk_var, nk_cl, part);
     return 0;
+}
+template <class T2>
+int launch_phase_moments_t(const T2* psi, long long cells, int n_slots, double weyl, double dV, double* var_a,
+                           double* phi2, double* part, double* out, cudaStream_t st) {
+    const int nb = moments_blocks(cells);
+    k_phase_moments<T2><<<nb, 256, 0, st>>>(psi, cells, n_slots, weyl, var_a, phi2, part);
+    k_finish_phase<<<1, 256, 0, st>>>(part, nb, dV, out);
+    return 0;
+}
+int launch_phase_moments(const float2* psi, long long cells, int n_slots, double weyl, double dV, double* var_a,
+                         double* phi2, double* part, double* out, cudaStream_t st) {
+    return launch_phase_moments_t(psi, cells, n_slots, weyl, dV, var_a, phi2, part, out, st);
+}
+int launch_phase_moments_f64(const double2* psi, long long cells, int n_slots, double weyl, double dV,
+                             double* var_a, double* phi2, double* part, double* out, cudaStream_t st) {
+    return launch_phase_moments_t(psi, cells, n_slots, weyl, dV, var_a, phi2, part, out, st);
 }
 int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, int nb_m, double dV,
                           double q_offset, double* scalars, int* err_word, cudaStream_t st) {

@@ -17,7 +17,7 @@ from . import _lib as L
 __all__ = [
     "TwaError", "twa_create", "twa_destroy", "twa_batch_elems", "twa_sample", "twa_step_batch",
     "twa_moments", "twa_run", "twa_sync_status", "twa_last_error", "twa_autotune",
-    "twa_last_launch_count", "twa_advance", "twa_advance_adaptive", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
+    "twa_last_launch_count", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
     "F64_PLAIN", "SCALAR_NAMES", "PASS_NAMES",
 ]
 
@@ -112,6 +112,14 @@ def twa_run(h, psi_cl, seed: int, n_steps: int, out_every: int, psi_work, series
 
 def twa_advance(h, psi, n_steps: int, out_every: int, series, stream=None) -> None:
     _check(_lib().twa_advance(h, _ptr(psi), int(n_steps), int(out_every), _ptr(series), _stream(stream)), h)
+
+
+def twa_phase_moments(h, inst: int, psi, var_a=None, phi2=None, totals=None, stream=None):
+    """Amplitude and phase variances (see include/twa.h); returns the device totals [Var A~, Var phi~]."""
+    if totals is None:
+        totals = torch.empty(2, dtype=torch.float64, device=psi.device)
+    _check(_lib().twa_phase_moments(h, int(inst), _ptr(psi), _ptr(var_a), _ptr(phi2), _ptr(totals), _stream(stream)), h)
+    return totals
 
 
 def twa_advance_adaptive(h, psi, n_out: int, out_every: int, c_f: float, series, stream=None):
