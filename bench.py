@@ -264,6 +264,33 @@ def _phase_moments_cost(ens, w, reps=3):
     return {"ms_per_call": ms, "GBps": nbytes / (ms * 1e-3) / 1e9, "var_a": float(tot[0]), "var_phi": float(tot[1])}
 
 
+def _particles_rate(ens, w, n_out=3):
+    """The bench batch advanced with one test particle per stream (Sec. III.D): the particle update
+    runs before every step, with the Poisson field brought to real space where the pipeline keeps
+    it spectral.  Reports the rate and the particles' spread after the timed interval."""
+    import numpy as np
+    import torch
+    from paper_2310_07119_gb300 import twa_advance, twa_particles_get, twa_particles_set
+    ns = STREAMS + 1
+    r0 = np.tile([0.5, 0.5, 0.5], (ns, 1))
+    ens.sample([w.psi_cl()], w.noise_seed)
+    twa_particles_set(ens.h, 0, r0, np.zeros((ns, 3)))
+    twa_advance(ens.h, ens.psi, OUT_EVERY, OUT_EVERY, ens.new_series(OUT_EVERY, OUT_EVERY))
+    series = ens.new_series(n_out * OUT_EVERY, OUT_EVERY)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    twa_advance(ens.h, ens.psi, n_out * OUT_EVERY, OUT_EVERY, series)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    r, p = twa_particles_get(ens.h, 0, ns, 3)
+    d = np.mod(r[1:] - r[0] + 0.5, 1.0) - 0.5
+    return {"value": STREAMS * w.grid.cells * OUT_EVERY * n_out / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / n_out,
+            "spread_x": float(np.sqrt(np.mean(np.sum((d - d.mean(0)) ** 2, 1)))),
+            "spread_p": float(np.sqrt(np.mean(np.sum((p[1:] - p[1:].mean(0)) ** 2, 1))))}
+
+
 def _one_d_rate():
     """The 1D workload (256 cells, 32 streams + classical, 1000 KDK steps, moments every 10): one
     on-chip launch per output interval on the FP32 path; the FP64 plain path on the same run."""
@@ -445,6 +472,7 @@ def run_twa(args):
         line["e2e"] = _e2e(ens, w)
         line["adaptive"] = _adaptive_rate(ens, w)
         line["phase_moments"] = _phase_moments_cost(ens, w)
+        line["particles"] = _particles_rate(ens, w)
         ens.close()
         torch.cuda.empty_cache()
         line["f64_plain"] = {"value": _f64_plain_rate(w), "unit": UNIT, "path": "TWA_F64_PLAIN, 1 stream + classical, 128^3"}

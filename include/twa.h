@@ -163,6 +163,19 @@ int twa_advance(twa_handle* h, void* psi, int n_steps, int out_every, double* se
 int twa_advance_adaptive(twa_handle* h, void* psi, int n_out, int out_every, double c_f, double* series,
                          double* times, void* stream);
 
+/* Test particles (Sec. III.D, Eq. cl_int): one particle per slot of instance `inst` (slot 0 moves
+   in the classical field's potential), dp/dt = -grad V_s(r), dr/dt = p (unit mass, normalized
+   units), advanced by every later twa_step_batch / twa_advance / twa_advance_adaptive / twa_run in
+   step with the field (leapfrog, half kicks merged like the field's).  grad V: the spectral
+   derivative of V on the grid along each axis (Nyquist mode excluded) at the grid points around r,
+   interpolated multilinearly; FP64 state and sums.  rp: HOST array [n_real + 1][6] = (r_x, r_y, r_z,
+   p_x, p_y, p_z); positions are wrapped into [0, L), unused axes ignored.  FP32 path only.  Set the
+   particles after twa_autotune (the tuner's timing steps would move them); the 1D path then runs
+   its on-chip steps one launch per step.  twa_particles_get synchronizes `stream`; it returns a
+   synchronized state after any of the calls above. */
+int twa_particles_set(twa_handle* h, int inst, const double* rp, void* stream);
+int twa_particles_get(twa_handle* h, int inst, double* rp, void* stream);
+
 /* Amplitude and phase variances of instance `inst` of a synchronized batch (Eq. varA, Eq. varPhi):
    per cell over the streams, A_s = |psi_s| with mean <A> and variance <dA^2>, and dphi_s =
    arg(psi_s conj(<psi>)) in (-pi, pi] (the phase relative to the ensemble-mean field; reference 0

@@ -53,6 +53,8 @@ _SIGS = {
     "twa_run": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "twa_advance": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "twa_phase_moments": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "twa_particles_set": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
+    "twa_particles_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "twa_advance_adaptive": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P,
                                             ctypes.POINTER(ctypes.c_double), _P]),
     "twa_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),

@@ -56,6 +56,9 @@ struct Inst {
     double* part_r = nullptr;
     double* part_m = nullptr;
     std::map<int, int> lines;  // (axis * 64 + op) -> lines per CTA
+    // test particles (FP32 path): state [n_slots][r 3, p 3] and the spectral derivative kernels
+    double* prt = nullptr;
+    double* dker[3] = {nullptr, nullptr, nullptr};
     // FP64 path
     double2* work64 = nullptr;
     double2* spec64 = nullptr;
@@ -450,12 +453,36 @@ int poisson_init(twa_handle* h, Inst& I, float2* psi, cudaStream_t st) {
 }
 
 // n steps; the first kick is the fraction a_first of a full kick (1/2 after a synchronized state).
+// Move the instance's test particles in the potential of the current batch: kick by kick_frac dt,
+// then drift by drift_frac dt.  Needs the Poisson field in real space: the axis pipeline keeps it
+// spectral along x between steps, so it is transformed back and forth around the update.
+int particles_step(twa_handle* h, Inst& I, float2* psi, double kick_frac, double drift_frac, cudaStream_t st) {
+    const bool v_spec = I.mode == MODE_3D;
+    if (v_spec) RC(run_pass(h, I, psi, 0, OP_INV, 0.0, I.vc, nullptr, I.n_pairs, st));
+    const double* ker[3] = {I.dker[0], I.dker[1] ? I.dker[1] : I.dker[0], I.dker[2] ? I.dker[2] : I.dker[0]};
+    launch_particles(I.vc, I.cells, I.n, I.dim, I.L, ker, h->p.C / (double)I.cells, kick_frac * h->p.dt,
+                     drift_frac * h->p.dt, I.n_slots, I.prt, st);
+    ++h->launches;
+    if (v_spec) RC(run_pass(h, I, psi, 0, OP_FWD, 0.0, I.vc, nullptr, I.n_pairs, st, 0, 0, 1.0f / (float)I.n[0]));
+    return 0;
+}
+
 int steps_f32(twa_handle* h, Inst& I, float2* psi, int n, double a_first, cudaStream_t st) {
     const int P = I.n_pairs;
     if (n <= 0) return 0;
-    if (I.mode == MODE_1D) return run_pass(h, I, psi, 0, OP_STEPS_1D, a_first, I.vc, nullptr, P, st, n);
+    if (I.mode == MODE_1D) {
+        if (!I.prt) return run_pass(h, I, psi, 0, OP_STEPS_1D, a_first, I.vc, nullptr, P, st, n);
+        // with test particles the on-chip steps run one at a time, the particles moving in between
+        for (int s = 0; s < n; ++s) {
+            const double k = (s == 0) ? a_first : 1.0;
+            RC(particles_step(h, I, psi, k, 1.0, st));
+            RC(run_pass(h, I, psi, 0, OP_STEPS_1D, k, I.vc, nullptr, P, st, 1));
+        }
+        return 0;
+    }
     for (int s = 0; s < n; ++s) {
         const double k = (s == 0) ? a_first : 1.0;
+        if (I.prt) RC(particles_step(h, I, psi, k, 1.0, st));
         if (I.mode == MODE_3DP) {
             RC(run_plane(h, I, psi, PL_KICK_DRIFT, k, st));
             RC(run_pass(h, I, psi, 2, OP_DRIFT_RHO, 0.0, I.vc, nullptr, P, st));
@@ -479,6 +506,7 @@ int steps_f32(twa_handle* h, Inst& I, float2* psi, int n, double a_first, cudaSt
 }
 
 int closing_kick(twa_handle* h, Inst& I, float2* psi, double frac, cudaStream_t st) {
+    if (I.prt) RC(particles_step(h, I, psi, frac, 0.0, st));
     if (I.mode == MODE_3D) return run_pass(h, I, psi, 0, OP_KICK_VINV, frac, I.vc, nullptr, I.n_pairs, st);
     float k, kl;
     split_kick(h, I, frac, k, kl);
@@ -1060,6 +1088,62 @@ int twa_advance(twa_handle* h, void* psi_work, int n_steps, int out_every, doubl
     total += h->launches;
     h->launches = total;
     CU(cudaGetLastError());
+    return TWA_OK;
+}
+
+int twa_particles_set(twa_handle* h, int inst, const double* rp, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!rp || inst < 0 || inst >= (int)h->in.size()) return fail(h, TWA_EINVAL, "twa_particles_set: bad argument");
+    if (h->p.precision != TWA_F32) return fail(h, TWA_EINVAL, "twa_particles_set: FP32 path only");
+    Inst& I = h->in[inst];
+    if (!I.prt) {
+        RC(dalloc(h, &I.prt, (size_t)I.n_slots * 6));
+        // derivative kernel of each axis: d(m) = (1/n) sum_k i k exp(i k m dx), Nyquist mode excluded
+        for (int a = 0; a < I.dim; ++a) {
+            const int n = I.n[a];
+            std::vector<double> d(n, 0.0);
+            for (int m = 0; m < n; ++m) {
+                double acc = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    if (n % 2 == 0 && j == n / 2) continue;
+                    const double k = wavenumber(j, n, I.L);
+                    acc -= k * std::sin(k * m * (I.L / n));
+                }
+                d[m] = acc / n;
+            }
+            RC(upload(h, &I.dker[a], d));
+        }
+    }
+    for (int s = 0; s < I.n_slots; ++s)
+        for (int a = 0; a < 6; ++a)
+            if (!std::isfinite(rp[6 * s + a])) return fail(h, TWA_EINVAL, "twa_particles_set: non-finite state");
+    std::vector<double> q(rp, rp + (size_t)6 * I.n_slots);
+    for (int s = 0; s < I.n_slots; ++s)
+        for (int a = 0; a < 3; ++a) {
+            if (a >= I.dim) {
+                q[6 * s + a] = 0.0;
+                q[6 * s + 3 + a] = 0.0;
+            } else {
+                q[6 * s + a] = std::fmod(q[6 * s + a], I.L);
+                if (q[6 * s + a] < 0.0) q[6 * s + a] += I.L;
+            }
+        }
+    CU(cudaMemcpyAsync(I.prt, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return TWA_OK;
+}
+
+int twa_particles_get(twa_handle* h, int inst, double* rp, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!rp || inst < 0 || inst >= (int)h->in.size()) return fail(h, TWA_EINVAL, "twa_particles_get: bad argument");
+    Inst& I = h->in[inst];
+    if (!I.prt) return fail(h, TWA_EINVAL, "twa_particles_get: no particles set on this instance");
+    cudaStream_t st = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(rp, I.prt, (size_t)I.n_slots * 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
     return TWA_OK;
 }
 

@@ -311,6 +311,69 @@ __global__ void k_max_abs(const float2* __restrict__ buf, long long n, unsigned*
     }
 }
 
+// Test particles (Sec. III.D, Eq. cl_int), one per slot: block s moves the particle of slot s,
+// prt[6 s + (0..2)] = r, prt[6 s + 3 + (0..2)] = p.  The force -grad V = (C / cells) grad W uses W, the
+// slot's real component of the packed Poisson field (real space): its spectral derivative along
+// each axis at the 2^dim grid points around r is a periodic convolution of the axis line with the
+// derivative kernel ker_a (one warp per corner and axis, FP64 sums), then interpolated multilinearly
+// to r.  p += force kick_dt, then r += p drift_dt, wrapped into [0, L).
+__global__ void k_particles(const float2* __restrict__ W, long long cells, int nx, int ny, int nz, int dim, double L,
+                            const double* __restrict__ kx, const double* __restrict__ ky,
+                            const double* __restrict__ kz, double fscale, double kick_dt, double drift_dt,
+                            double* prt) {
+    const int s = blockIdx.x;
+    const float* Wc = reinterpret_cast<const float*>(W + (long long)(s >> 1) * cells) + (s & 1);
+    double* q = prt + 6 * s;
+    const int n[3] = {nx, ny, nz};
+    const long long stride[3] = {1, nx, (long long)nx * ny};
+    __shared__ double D[8][3];
+    __shared__ int i0[3];
+    __shared__ double fr[3];
+    if (threadIdx.x < dim) {
+        const int a = threadIdx.x;
+        const double sc = q[a] / (L / n[a]);
+        const double fl = floor(sc);
+        long long i = (long long)fl % n[a];
+        if (i < 0) i += n[a];
+        i0[a] = (int)i;
+        fr[a] = sc - fl;
+    }
+    __syncthreads();
+    const int nc = 1 << dim;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int pr = warp; pr < nc * dim; pr += nw) {
+        const int c = pr / dim, a = pr % dim;
+        int j[3] = {0, 0, 0};
+        for (int b = 0; b < dim; ++b) j[b] = (i0[b] + ((c >> b) & 1)) % n[b];
+        const long long base = j[0] + (long long)nx * (j[1] + (long long)ny * j[2]) - (long long)j[a] * stride[a];
+        const double* ker = a == 0 ? kx : (a == 1 ? ky : kz);
+        double acc = 0.0;
+        for (int m = lane; m < n[a]; m += 32) {
+            int d = j[a] - m;
+            if (d < 0) d += n[a];
+            acc += ker[d] * (double)Wc[2 * (base + (long long)m * stride[a])];
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) D[c][a] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < dim; ++a) {
+            double g = 0.0;
+            for (int c = 0; c < nc; ++c) {
+                double w = 1.0;
+                for (int b = 0; b < dim; ++b) w *= ((c >> b) & 1) ? fr[b] : 1.0 - fr[b];
+                g += w * D[c][a];
+            }
+            const double p = q[3 + a] + fscale * g * kick_dt;
+            double r = fmod(q[a] + p * drift_dt, L);
+            if (r < 0.0) r += L;
+            q[3 + a] = p;
+            q[a] = r;
+        }
+    }
+}
+
 // Sum the per-block partials in block order and form the TWA_NSCALARS scalars of one instance.
 __global__ void k_finish_scalars(const double* __restrict__ part_r, int nb_r, const double* __restrict__ part_m,
                                  int nb_m, double dV, double q_offset, double* scalars, int* err_word) {
@@ -416,6 +479,12 @@ int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, 
 int launch_max_abs(const float2* buf, long long n, unsigned* vmax, cudaStream_t st) {
     const long long b = (n + 255) / 256;
     k_max_abs<<<(int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8), 256, 0, st>>>(buf, n, vmax);
+    return 0;
+}
+int launch_particles(const float2* W, long long cells, const int* n, int dim, double L, const double* const* ker,
+                     double fscale, double kick_dt, double drift_dt, int n_slots, double* prt, cudaStream_t st) {
+    k_particles<<<n_slots, 128, 0, st>>>(W, cells, n[0], n[1], n[2], dim, L, ker[0], ker[1], ker[2], fscale, kick_dt,
+                                         drift_dt, prt);
     return 0;
 }
 int launch_store_series(const double* cur, double* series, int* counter, int n, cudaStream_t st) {

@@ -17,7 +17,7 @@ from . import _lib as L
 __all__ = [
     "TwaError", "twa_create", "twa_destroy", "twa_batch_elems", "twa_sample", "twa_step_batch",
     "twa_moments", "twa_run", "twa_sync_status", "twa_last_error", "twa_autotune",
-    "twa_last_launch_count", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
+    "twa_last_launch_count", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_particles_set", "twa_particles_get", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
     "F64_PLAIN", "SCALAR_NAMES", "PASS_NAMES",
 ]
 
@@ -112,6 +112,26 @@ def twa_run(h, psi_cl, seed: int, n_steps: int, out_every: int, psi_work, series
 
 def twa_advance(h, psi, n_steps: int, out_every: int, series, stream=None) -> None:
     _check(_lib().twa_advance(h, _ptr(psi), int(n_steps), int(out_every), _ptr(series), _stream(stream)), h)
+
+
+def twa_particles_set(h, inst: int, r, p, stream=None) -> None:
+    """Test particles of instance ``inst`` (see include/twa.h): r, p of shape (n_real + 1, dim)."""
+    import numpy as np
+    r, p = np.asarray(r, dtype=np.float64), np.asarray(p, dtype=np.float64)
+    q = np.zeros((r.shape[0], 6))
+    q[:, :r.shape[1]] = r
+    q[:, 3:3 + p.shape[1]] = p
+    buf = (ctypes.c_double * q.size)(*q.ravel())
+    _check(_lib().twa_particles_set(h, int(inst), buf, _stream(stream)), h)
+
+
+def twa_particles_get(h, inst: int, n_slots: int, dim: int, stream=None):
+    """(r, p) of instance ``inst``, each (n_slots, dim), synchronized."""
+    import numpy as np
+    buf = (ctypes.c_double * (6 * n_slots))()
+    _check(_lib().twa_particles_get(h, int(inst), buf, _stream(stream)), h)
+    q = np.array(buf[:]).reshape(n_slots, 6)
+    return q[:, :dim].copy(), q[:, 3:3 + dim].copy()
 
 
 def twa_phase_moments(h, inst: int, psi, var_a=None, phi2=None, totals=None, stream=None):
