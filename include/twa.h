@@ -170,8 +170,9 @@ int twa_advance_adaptive(twa_handle* h, void* psi, int n_out, int out_every, dou
    derivative of V on the grid along each axis (Nyquist mode excluded) at the grid points around r,
    interpolated multilinearly; FP64 state and sums.  rp: HOST array [n_real + 1][6] = (r_x, r_y, r_z,
    p_x, p_y, p_z); positions are wrapped into [0, L), unused axes ignored.  FP32 path only.  Set the
-   particles after twa_autotune (the tuner's timing steps would move them); the 1D path then runs
-   its on-chip steps one launch per step.  twa_particles_get synchronizes `stream`; it returns a
+   particles after twa_autotune (the tuner's timing steps would move them; setting them also moves
+   a 3D instance with square xy planes to the plane pipeline, whose potential is real between
+   steps); the 1D path then runs its on-chip steps one launch per step.  twa_particles_get synchronizes `stream`; it returns a
    synchronized state after any of the calls above. */
 int twa_particles_set(twa_handle* h, int inst, const double* rp, void* stream);
 int twa_particles_get(twa_handle* h, int inst, double* rp, void* stream);

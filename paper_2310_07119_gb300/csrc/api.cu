@@ -1129,6 +1129,10 @@ int twa_particles_set(twa_handle* h, int inst, const double* rp, void* stream) {
             }
         }
     CU(cudaMemcpyAsync(I.prt, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    // the particles need the potential in real space before every step: the plane pipeline keeps it
+    // so, the axis pipeline would transform it back and forth each step (every call restarts the
+    // Poisson field from the batch, so the switch is safe between calls)
+    if (I.mode == MODE_3D && I.n[0] == I.n[1] && I.n[0] >= 16 && I.n[0] <= 256) I.mode = MODE_3DP;
     if (h->gexec) {
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
