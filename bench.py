@@ -50,6 +50,8 @@ def _args():
     ap.add_argument("--no-extras", action="store_true", help="skip cpu/f64/cufft/e2e side measurements")
     ap.add_argument("--streams", type=int, default=STREAMS, help="streams per batch (smaller batches for ncu captures)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default pass shapes, axis pipeline)")
+    ap.add_argument("--paper-scale", action="store_true",
+                    help="only measure the 512^3 x 64-stream soliton (about 175 GB on the device) and print it")
     return ap.parse_args()
 
 
@@ -505,8 +507,35 @@ def _ncu_traffic(kernel_op: str):
         return None
 
 
+def _paper_scale(steps=2):
+    """512^3 x 64 streams of the stable-object (soliton) workload, default pass shapes."""
+    import torch
+    import twa_inputs as ti
+    from paper_2310_07119_gb300 import Ensemble, twa_advance
+    w = ti.workload_3d_soliton(512, 64, 4000)
+    ens = Ensemble([w.grid], w.phys.hbar_m, w.phys.C, w.phys.dt, w.phys.n_tot, [64], want_modes=True)
+    ens.sample([w.psi_cl()], w.noise_seed)
+    twa_advance(ens.h, ens.psi, OUT_EVERY, OUT_EVERY, ens.new_series(OUT_EVERY, OUT_EVERY))
+    series = ens.new_series(steps * OUT_EVERY, OUT_EVERY)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    twa_advance(ens.h, ens.psi, steps * OUT_EVERY, OUT_EVERY, series)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": "3D soliton 512^3 x 64 streams (+ classical field), moments every 10 steps, default pass shapes",
+           "value": 64 * w.grid.cells * OUT_EVERY * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+           "batch_bytes": int(ens.psi.numel() * 8), "device_bytes_reserved": int(torch.cuda.memory_reserved())}
+    ens.close()
+    return out
+
+
 def main():
     args = _args()
+    if args.paper_scale:
+        print(json.dumps({"paper_scale": _paper_scale()}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -1,0 +1,54 @@
+"""Paper-scale cases on the GPU path: the Q relation of Eq. Q_relation (n_s Q_s independent of the
+simulated particle number while Q << 1) on the 1D cosine overdensity at hbar/m = 2.5e-4 with 1024
+streams, checked against the oracle; and 3D grids whose x lines are 512 to 2048 long."""
+import numpy as np
+import pytest
+import torch
+
+import twa_inputs as ti
+from oracle import twa
+from tests.gpu_common import field_rel_l2, make_ensemble, oracle_batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_q_relation_on_the_1d_cosine_collapse():
+    g = ti.Grid.cube(1, 512)
+    hb = 2.5e-4
+    dt = ti.dt_pi4_rule(g, hb)
+    n_steps, every, ns = 200, 50, 1024
+    out = {}
+    for n_tot in (1e8, 1e10):
+        w = ti.Workload("cosine", g, ti.Physics(hb, ti.C_UNIT, dt, n_tot), ns, n_steps, every, 0, 2023)
+        cl = w.psi_cl()
+        ens = make_ensemble([w], 0, want_modes=False)
+        series = ens.run([cl], w.noise_seed, n_steps, every).cpu().numpy()
+        q = series[:, 0, 0]
+        out[n_tot] = n_tot * (q - q[0])
+        if n_tot == 1e8:
+            _, ref, _ = twa.run(cl, hb, ti.C_UNIT, dt, 1.0, 1, n_tot, ns, w.noise_seed, n_steps, every,
+                                with_modes=False)
+            qr = np.array([s["Q"] for s in ref])
+            ref_scaled = n_tot * (qr - qr[0])
+            assert np.all(np.abs(out[n_tot][1:] - ref_scaled[1:]) <= 0.02 * np.abs(ref_scaled[1:]) + 1e-6)
+        ens.close()
+    assert out[1e8][-1] > 0
+    assert np.all(np.abs(out[1e10][1:] - out[1e8][1:]) <= 0.05 * np.abs(out[1e10][1:]))
+
+
+@pytest.mark.parametrize("n", [512, 1024, 2048])
+def test_long_x_lines_in_3d(n):
+    w = ti.Workload("kgauss", ti.Grid(3, (n, 8, 8), 1.0), ti.Physics(ti.HBAR_3D, ti.C_UNIT, 1e-5, 1e8), 2, 10, 5, 5, 31)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    ens.sample([cl], w.noise_seed)
+    ens.step(w.n_steps)
+    got = ens.fields(0).cpu().numpy().astype(np.complex128)
+    assert np.all(field_rel_l2(got, oracle_batch(w, cl, w.n_steps), 3) < 1e-4)
+    ens.close()
