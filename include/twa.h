@@ -210,7 +210,7 @@ int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_m
    params: psi is the caller's synchronized batch of n_real + 1 fields of grid->n[0] cells (float2,
    slot 0 = classical field), advanced in place by n_steps KDK steps on `stream`.  No handle is
    used: the Poisson buffer and the FFT and phase tables live in static device arrays of the
-   library (TWA_STATIC_SCRATCH_ELEMS complex values plus about 72 KB of tables), held by every GPU
+   library (TWA_STATIC_SCRATCH_ELEMS complex values plus about 106 KB of tables), held by every GPU
    that loads the library until the process exits.  The first call on a device looks up the device
    addresses of those arrays (make that first call before any stream capture).  Every call
    rebuilds the tables and the Poisson field; calls whose work overlaps on the GPU share the arrays
