@@ -9,6 +9,11 @@
 //   3D : x [iFFT_x of V + kick + drift_x] -> y [drift_y] -> z [drift_z + density + FFT_z]
 //        -> x [FFT_x] -> y [FFT_y, Poisson, iFFT_y] -> z [iFFT_z]                   (6 passes/step)
 //        V stays spectral along x between steps; its inverse is fused into the next kick.
+//   3D, square xy planes (plane pipeline): [kick + drift_x + drift_y per z-plane] -> z [drift_z +
+//        density + FFT_z] -> [FFT_xy, Poisson, iFFT_xy per plane] -> z [iFFT_z]    (4 passes/step)
+//        The autotuner times both 3D pipelines and keeps the axis one on near-ties.
+// Around these: adaptive steps (the Delta t rule read back before each output interval), test
+// particles moved before every step, and the amplitude/phase moments on request.
 #include <cuda_runtime.h>
 
 #include <algorithm>
