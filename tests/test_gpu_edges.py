@@ -123,3 +123,36 @@ def test_literal_noise_reading_samples_match_oracle(precision):
     # same normals, sigma scaled by sqrt(2) (up to the rounding of the stored fields)
     atol = 4 * np.finfo(np.float32).eps * amp if precision == 0 else 1e-13 * amp
     assert np.max(np.abs(out[1] - np.sqrt(2.0) * out[0])) <= atol
+
+
+def test_added_entry_points_reject_bad_use():
+    from paper_2310_07119_gb300 import (twa_advance_adaptive, twa_particles_get, twa_particles_set,
+                                        twa_phase_moments)
+    w = ti.small_workload("kgauss", 3, 16, 2, 0, n_tot=1e8)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0)
+    ens.sample([cl], w.noise_seed)
+    s = ens.new_series(10, 5)
+    for bad in (dict(c_f=0.0), dict(c_f=-1.0), dict(c_f=float("nan"))):
+        with pytest.raises(TwaError) as e:
+            twa_advance_adaptive(ens.h, ens.psi, 2, 5, bad["c_f"], s)
+        assert e.value.code == L.TWA_EINVAL
+    with pytest.raises(TwaError) as e:
+        twa_particles_get(ens.h, 0, 3, 3)                 # nothing set yet
+    assert e.value.code == L.TWA_EINVAL
+    with pytest.raises(TwaError) as e:
+        twa_particles_set(ens.h, 0, np.full((3, 3), np.nan), np.zeros((3, 3)))
+    assert e.value.code == L.TWA_EINVAL
+    with pytest.raises(TwaError) as e:
+        twa_phase_moments(ens.h, 5, ens.psi)              # no such instance
+    assert e.value.code == L.TWA_EINVAL
+    ens.close()
+    e64 = make_ensemble([w], 1)
+    e64.sample([cl], w.noise_seed)
+    with pytest.raises(TwaError) as e:
+        twa_advance_adaptive(e64.h, e64.psi, 1, 5, 0.01, e64.new_series(5, 5))
+    assert e.value.code == L.TWA_EINVAL and "FP32" in str(e.value)
+    with pytest.raises(TwaError) as e:
+        twa_particles_set(e64.h, 0, np.zeros((3, 3)), np.zeros((3, 3)))
+    assert e.value.code == L.TWA_EINVAL
+    e64.close()
