@@ -493,7 +493,8 @@ def run_twa(args):
 
 
 def _ncu_traffic(kernel_op: str):
-    """DRAM bytes per launch of the dominant pass from a committed ncu summary, if it matches this build."""
+    """DRAM bytes per launch of the dominant pass from a committed ncu summary, if it was taken on the
+    current kernel sources."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None

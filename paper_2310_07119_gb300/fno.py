@@ -8,7 +8,7 @@ input ensemble of a few streams and an independent reference ensemble — evolve
 few-stream estimate n_est and the reference n_ref.  The target is the correction spectrum
 <n_k> - n_k^cl relative to n_cl + n_tot / K (K modes); the surrogate's job is to predict the many-stream value
 from the classical spectrum and the few-stream estimate, and the full ensemble stays the fallback and
-the judge of its error.
+the reference for its error.
 """
 from __future__ import annotations
 
