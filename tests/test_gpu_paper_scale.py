@@ -52,3 +52,30 @@ def test_long_x_lines_in_3d(n):
     got = ens.fields(0).cpu().numpy().astype(np.complex128)
     assert np.all(field_rel_l2(got, oracle_batch(w, cl, w.n_steps), 3) < 1e-4)
     ens.close()
+
+
+def test_soliton_256_cubed_sampled_streams():
+    """The stable-object workload at its full layout (256^3 cells x 65 slots, 8.7 GB of FP32 fields), 10 KDK steps:
+    the classical field and two sampled streams against the oracle."""
+    from oracle import sp
+    from oracle.philox import wigner_normals
+    w = ti.workload_3d_soliton(256, 64, 10)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0, want_modes=False)
+    ens.sample([cl], w.noise_seed)
+    ens.step(w.n_steps)
+    slots = [0, 1, 64]
+    sub = ens.fields(0)[slots].cpu().numpy().astype(np.complex128)
+    ens.close()
+    torch.cuda.empty_cache()
+    sig = twa.noise_sigma(w.phys.n_tot, w.grid.dV, w.phys.noise_conv)
+    ref = np.empty((len(slots),) + cl.shape, dtype=np.complex128)
+    for j, s_ in enumerate(slots):
+        if s_ == 0:
+            ref[j] = cl
+        else:
+            zr, zi = wigner_normals(w.noise_seed, cl.size, s_)
+            ref[j] = cl + sig * (zr + 1j * zi).reshape(cl.shape)
+    for _ in range(w.n_steps):
+        ref = sp.step(ref, w.phys.hbar_m, w.phys.C, w.phys.dt, w.grid.L, 3)
+    assert np.all(field_rel_l2(sub, ref, 3) < 1e-4), field_rel_l2(sub, ref, 3)
