@@ -60,6 +60,13 @@ struct PassArgs {
     const float4* ph2;      // plane passes: kinetic phase along y (hi, lo)
 };
 
+// Asks L2 to fetch a byte range ahead of its use (a hint: nothing waits on it, no data returns).
+// The range must lie inside one allocation, start on 16 bytes and span a multiple of 16 bytes.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes)
+                 : "memory");
+}
+
 // z * exp(-i theta).  For |theta| <= 1/4 (every kick of the measured workloads) sin and cos are
 // their Taylor polynomials through theta^7 and theta^8 (truncation below 1e-11, so the result is
 // correctly rounded to float up to the rounding of the evaluation); otherwise theta is reduced to
@@ -86,7 +93,7 @@ __device__ __forceinline__ float2 kick_w(float2 z, float k_hi, float k_lo, float
 
 // At least 512 resident threads (16 warps) per SM so that one CTA's loads overlap another's
 // transforms; this caps the registers per thread at 128.
-constexpr int min_ctas(int threads) { return threads >= 512 ? 1 : 512 / threads; }
+constexpr int min_ctas(int threads) { return threads >= 512 ? 1 : (512 / threads < 32 ? 512 / threads : 32); }
 
 // Ops that keep a per-thread array across the two streams of a pair park it in a thread-private
 // shared-memory stash (2 RMAX floats per thread, after the exchange lines) instead of registers.
@@ -151,6 +158,35 @@ k_line(const PassArgs a) {
     const int S = STRIDED ? a.S : 1;
     const int f = blockIdx.y;
     float2 v[RMAX];
+
+    // Pair passes other than kick_drift_vinv ask L2 for the pair's stream lines that are read after
+    // another field (the potential, or the first stream): their DRAM latency then overlaps the first
+    // field's transforms.  kick_drift_vinv was measured slower with it.
+    constexpr bool PF = OP == OP_KICK_DRIFT || OP == OP_KICK_FWD_OUT || OP == OP_KICK_VINV ||
+                        OP == OP_DRIFT_RHO || OP == OP_RHO_FWD;
+    if constexpr (PF) {
+        auto prefetch_lines = [&](const float2* F) {
+            if constexpr (STRIDED) {
+                const int tq = (a.Qn + LINES - 1) / LINES;
+                const int q0 = (int)(blockIdx.x % tq) * LINES;
+                const unsigned bytes = (unsigned)min(LINES, a.Qn - q0) * 8u;
+                const float2* b0 = F + q0 + (long long)(blockIdx.x / tq) * a.OS;
+                for (int j = tid; j < N; j += NTH) {
+                    const float2* p = b0 + (long long)j * S;
+                    if (((reinterpret_cast<uintptr_t>(p) | bytes) & 15u) == 0) prefetch_l2(p, bytes);
+                }
+            } else {
+                const int r0 = (int)blockIdx.x * LINES;
+                const unsigned bytes = (unsigned)min(LINES, (int)(a.cells / N) - r0) * N * 8u;
+                const char* b0 = reinterpret_cast<const char*>(F + (long long)r0 * N);
+                if (((reinterpret_cast<uintptr_t>(b0) | bytes) & 15u) == 0)
+                    for (unsigned o = (unsigned)tid * 4096u; o < bytes; o += NTH * 4096u)
+                        prefetch_l2(b0 + o, min(4096u, bytes - o));
+            }
+        };
+        if (OP != OP_DRIFT_RHO && OP != OP_RHO_FWD) prefetch_lines(a.psi + (long long)(2 * f) * a.cells);
+        if (2 * f + 1 < a.n_slots) prefetch_lines(a.psi + (long long)(2 * f + 1) * a.cells);
+    }
 
     // field data is read once per pass: load it through L2 only (ld.global.cg), so the twiddle,
     // phase and k^2 tables keep the L1 cache
