@@ -159,34 +159,32 @@ k_line(const PassArgs a) {
     const int f = blockIdx.y;
     float2 v[RMAX];
 
-    // Pair passes other than kick_drift_vinv ask L2 for the pair's stream lines that are read after
-    // another field (the potential, or the first stream): their DRAM latency then overlaps the first
-    // field's transforms.  kick_drift_vinv was measured slower with it.
-    constexpr bool PF = OP == OP_KICK_DRIFT || OP == OP_KICK_FWD_OUT || OP == OP_KICK_VINV ||
-                        OP == OP_DRIFT_RHO || OP == OP_RHO_FWD;
-    if constexpr (PF) {
-        auto prefetch_lines = [&](const float2* F) {
-            if constexpr (STRIDED) {
-                const int tq = (a.Qn + LINES - 1) / LINES;
-                const int q0 = (int)(blockIdx.x % tq) * LINES;
-                const unsigned bytes = (unsigned)min(LINES, a.Qn - q0) * 8u;
-                const float2* b0 = F + q0 + (long long)(blockIdx.x / tq) * a.OS;
-                for (int j = tid; j < N; j += NTH) {
-                    const float2* p = b0 + (long long)j * S;
-                    if (((reinterpret_cast<uintptr_t>(p) | bytes) & 15u) == 0) prefetch_l2(p, bytes);
-                }
-            } else {
-                const int r0 = (int)blockIdx.x * LINES;
-                const unsigned bytes = (unsigned)min(LINES, (int)(a.cells / N) - r0) * N * 8u;
-                const char* b0 = reinterpret_cast<const char*>(F + (long long)r0 * N);
-                if (((reinterpret_cast<uintptr_t>(b0) | bytes) & 15u) == 0)
-                    for (unsigned o = (unsigned)tid * 4096u; o < bytes; o += NTH * 4096u)
-                        prefetch_l2(b0 + o, min(4096u, bytes - o));
+    // The pair passes ask L2 for the stream lines they read after another field (the potential, or
+    // the first stream) right after that field's loads are issued: the hint queues behind those
+    // loads, and the stream's DRAM latency then overlaps the first field's transforms.
+    auto prefetch_lines = [&](const float2* F) {
+        if constexpr (STRIDED) {
+            const int tq = (a.Qn + LINES - 1) / LINES;
+            const int q0 = (int)(blockIdx.x % tq) * LINES;
+            const unsigned bytes = (unsigned)min(LINES, a.Qn - q0) * 8u;
+            const float2* b0 = F + q0 + (long long)(blockIdx.x / tq) * a.OS;
+            for (int j = tid; j < N; j += NTH) {
+                const float2* p = b0 + (long long)j * S;
+                if (((reinterpret_cast<uintptr_t>(p) | bytes) & 15u) == 0) prefetch_l2(p, bytes);
             }
-        };
-        if (OP != OP_DRIFT_RHO && OP != OP_RHO_FWD) prefetch_lines(a.psi + (long long)(2 * f) * a.cells);
+        } else {
+            const int r0 = (int)blockIdx.x * LINES;
+            const unsigned bytes = (unsigned)min(LINES, (int)(a.cells / N) - r0) * N * 8u;
+            const char* b0 = reinterpret_cast<const char*>(F + (long long)r0 * N);
+            if (((reinterpret_cast<uintptr_t>(b0) | bytes) & 15u) == 0)
+                for (unsigned o = (unsigned)tid * 4096u; o < bytes; o += NTH * 4096u)
+                    prefetch_l2(b0 + o, min(4096u, bytes - o));
+        }
+    };
+    auto prefetch_pair = [&](bool first) {
+        if (first) prefetch_lines(a.psi + (long long)(2 * f) * a.cells);
         if (2 * f + 1 < a.n_slots) prefetch_lines(a.psi + (long long)(2 * f + 1) * a.cells);
-    }
+    };
 
     // field data is read once per pass: load it through L2 only (ld.global.cg), so the twiddle,
     // phase and k^2 tables keep the L1 cache
@@ -244,8 +242,9 @@ k_line(const PassArgs a) {
         // the pair's real potentials are read once and parked in the stash as two float planes
         float* stv = reinterpret_cast<float*>(smem + LINES * LS) + tid;
         const bool kick = a.kick != 0.f;
+        if (kick) load_nat(v, a.buf + (long long)f * a.cells);
+        prefetch_pair(kick);
         if (kick) {
-            load_nat(v, a.buf + (long long)f * a.cells);
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) {
                 stv[i * NTH] = v[i].x;
@@ -274,6 +273,7 @@ k_line(const PassArgs a) {
     } else if constexpr (OP == OP_KICK_DRIFT_VINV || OP == OP_KICK_VINV) {
         // inverse transform of the pair's Poisson line, parked in the stash for both streams
         load_spec(v, a.buf + (long long)f * a.cells);
+        prefetch_pair(true);
         fft_line<N, true, WARP, MASK, TS>(v, t, sm, tw);
         // the two streams' potentials as separate float planes (each stream reads only its own)
         float* stv = reinterpret_cast<float*>(smem + LINES * LS) + tid;
@@ -304,6 +304,7 @@ k_line(const PassArgs a) {
             if (slot < a.n_slots) {
                 float2* F = a.psi + (long long)slot * a.cells;
                 load_nat(v, F);
+                if (h == 0) prefetch_pair(false);
                 if constexpr (OP == OP_DRIFT_RHO) {
                     drift(v);
                     store_nat(v, F);
