@@ -66,6 +66,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes)
                  : "memory");
 }
+// The same for the cache sector holding one address, as an ordinary per-thread instruction.
+__device__ __forceinline__ void prefetch_l2_sector(const void* p) { asm volatile("prefetch.L2 [%0];" ::"l"(p)); }
 
 // z * exp(-i theta).  For |theta| <= 1/4 (every kick of the measured workloads) sin and cos are
 // their Taylor polynomials through theta^7 and theta^8 (truncation below 1e-11, so the result is
@@ -168,9 +170,10 @@ k_line(const PassArgs a) {
             const int q0 = (int)(blockIdx.x % tq) * LINES;
             const unsigned bytes = (unsigned)min(LINES, a.Qn - q0) * 8u;
             const float2* b0 = F + q0 + (long long)(blockIdx.x / tq) * a.OS;
+            // one short segment per position: plain per-thread prefetches, one per 32-byte sector
             for (int j = tid; j < N; j += NTH) {
-                const float2* p = b0 + (long long)j * S;
-                if (((reinterpret_cast<uintptr_t>(p) | bytes) & 15u) == 0) prefetch_l2(p, bytes);
+                const char* p = reinterpret_cast<const char*>(b0 + (long long)j * S);
+                for (unsigned o = 0; o < bytes; o += 32u) prefetch_l2_sector(p + o);
             }
         } else {
             const int r0 = (int)blockIdx.x * LINES;
