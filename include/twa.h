@@ -46,6 +46,10 @@ extern "C" {
 #define TWA_ETIMEOUT    -4   /* a device-side wait gave up (reported through twa_sync_status) */
 #define TWA_ENONFINITE  -5   /* a moments pass met a non-finite field value */
 
+/* Alignment: the calls that take a handle return TWA_EINVAL when a field buffer (psi, psi_cl,
+   psi_work) does not start on a 16-byte boundary; cudaMalloc and PyTorch allocations do.  Other
+   device pointers need the alignment of their element type. */
+
 #define TWA_F32          0   /* batched FP32 path: fused Stockham passes, realization pairs */
 #define TWA_F64_PLAIN    1   /* comparator: complex128, one realization per launch, no fusion */
 

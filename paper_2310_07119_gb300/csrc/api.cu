@@ -135,6 +135,11 @@ int fail(twa_handle* h, int code, const std::string& msg) {
     return code;
 }
 
+// Field buffers are read with 16-byte copies (cp.async in the pipelined passes, double2 loads of
+// the classical field): their base addresses must be 16-byte aligned.  Instances and slots start
+// on 64-byte multiples inside a batch (every axis has at least 8 cells), so the base decides.
+bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
 #define CU(call)                                                                          \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
@@ -856,6 +861,7 @@ size_t twa_batch_elems(const twa_handle* h) {
 int twa_sample(twa_handle* h, const void* psi_cl, uint64_t seed, void* psi, void* stream) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     if (!psi_cl || !psi) return fail(h, TWA_EINVAL, "twa_sample: null buffer");
+    if (misaligned(psi_cl) || misaligned(psi)) return fail(h, TWA_EINVAL, "twa_sample: buffers must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     h->launches = 0;
     size_t cl_off = 0;
@@ -878,6 +884,7 @@ int twa_sample(twa_handle* h, const void* psi_cl, uint64_t seed, void* psi, void
 int twa_step_batch(twa_handle* h, void* psi, int n_steps, void* stream) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     if (!psi || n_steps < 0) return fail(h, TWA_EINVAL, "twa_step_batch: bad argument");
+    if (misaligned(psi)) return fail(h, TWA_EINVAL, "twa_step_batch: psi must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     h->launches = 0;
     if (n_steps == 0) return TWA_OK;
@@ -904,6 +911,7 @@ int twa_step_batch(twa_handle* h, void* psi, int n_steps, void* stream) {
 int twa_moments(twa_handle* h, int inst, const void* psi, const twa_moments_out* out, void* stream) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     if (!psi || !out || inst < 0 || inst >= (int)h->in.size()) return fail(h, TWA_EINVAL, "twa_moments: bad argument");
+    if (misaligned(psi)) return fail(h, TWA_EINVAL, "twa_moments: psi must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     h->launches = 0;
     Inst& I = h->in[inst];
@@ -1013,6 +1021,7 @@ int twa_advance(twa_handle* h, void* psi_work, int n_steps, int out_every, doubl
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     if (!psi_work || !series || out_every <= 0 || n_steps < 0 || n_steps % out_every)
         return fail(h, TWA_EINVAL, "twa_advance: bad argument (n_steps must be a multiple of out_every)");
+    if (misaligned(psi_work)) return fail(h, TWA_EINVAL, "twa_advance: psi must be 16-byte aligned");
     cudaStream_t user = (cudaStream_t)stream;
     long long total = 0;
     h->launches = 0;
@@ -1161,6 +1170,7 @@ int twa_phase_moments(twa_handle* h, int inst, const void* psi, double* var_a, d
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     if (!psi || !totals || inst < 0 || inst >= (int)h->in.size())
         return fail(h, TWA_EINVAL, "twa_phase_moments: bad argument");
+    if (misaligned(psi)) return fail(h, TWA_EINVAL, "twa_phase_moments: psi must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     Inst& I = h->in[inst];
     const double weyl = 1.0 / (2.0 * h->p.n_tot * I.dV);
@@ -1181,6 +1191,7 @@ int twa_advance_adaptive(twa_handle* h, void* psi_work, int n_out, int out_every
     if (!psi_work || !series || !times || n_out < 0 || out_every <= 0 || !(c_f > 0.0))
         return fail(h, TWA_EINVAL, "twa_advance_adaptive: bad argument (need n_out >= 0, out_every > 0, c_f > 0)");
     if (h->p.precision != TWA_F32) return fail(h, TWA_EINVAL, "twa_advance_adaptive: FP32 path only");
+    if (misaligned(psi_work)) return fail(h, TWA_EINVAL, "twa_advance_adaptive: psi must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     const double dt0 = h->p.dt;
     long long total = 0;
@@ -1434,6 +1445,7 @@ int tune_passes(twa_handle* h, Inst& I, float2* f, const std::vector<TunePass>& 
 extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, void* stream) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     if (!psi) return fail(h, TWA_EINVAL, "twa_autotune: null buffer");
+    if (misaligned(psi)) return fail(h, TWA_EINVAL, "twa_autotune: psi must be 16-byte aligned");
     if (h->p.precision != TWA_F32) return TWA_OK;
     cudaStream_t st = (cudaStream_t)stream;
     std::map<std::string, int> cache = read_cache(cache_path);

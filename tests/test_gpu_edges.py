@@ -156,3 +156,33 @@ def test_added_entry_points_reject_bad_use():
         twa_particles_set(e64.h, 0, np.zeros((3, 3)), np.zeros((3, 3)))
     assert e.value.code == L.TWA_EINVAL
     e64.close()
+
+
+def test_calls_reject_a_batch_that_is_not_16_byte_aligned():
+    """Field buffers are read with 16-byte copies; a batch view starting 8 bytes into an allocation
+    is refused with TWA_EINVAL before anything is launched, and the aligned batch is untouched."""
+    from paper_2310_07119_gb300 import (twa_advance_adaptive, twa_autotune, twa_moments, twa_phase_moments,
+                                        twa_step_batch)
+    w = ti.small_workload("kgauss", 3, 16, 2, 0, n_tot=1e8)
+    ens = make_ensemble([w], 0)
+    ens.sample([w.psi_cl()], w.noise_seed)
+    before = ens.psi.clone()
+    raw = torch.zeros(ens.psi.numel() + 1, dtype=ens.psi.dtype, device=ens.psi.device)
+    off = raw[1:]
+    off.copy_(ens.psi)
+    assert off.data_ptr() % 16 == 8
+    calls = {
+        "twa_step_batch": lambda: twa_step_batch(ens.h, off, 1),
+        "twa_advance": lambda: twa_advance(ens.h, off, 10, 10, ens.new_series(10, 10)),
+        "twa_moments": lambda: twa_moments(ens.h, 0, off, {}),
+        "twa_phase_moments": lambda: twa_phase_moments(ens.h, 0, off),
+        "twa_advance_adaptive": lambda: twa_advance_adaptive(ens.h, off, 1, 5, 0.01, ens.new_series(5, 5)),
+        "twa_autotune": lambda: twa_autotune(ens.h, off),
+    }
+    for name, call in calls.items():
+        with pytest.raises(TwaError) as e:
+            call()
+        assert e.value.code == L.TWA_EINVAL and "16-byte" in str(e.value) and name in str(e.value), name
+    torch.cuda.synchronize()
+    assert torch.equal(off, before) and torch.equal(ens.psi, before)
+    ens.close()
