@@ -285,6 +285,12 @@ int twa_autotune(twa_handle* h, void* psi, const char* cache_path, void* stream)
 /* Number of kernel launches the last twa_step_batch / twa_run / twa_moments call enqueued. */
 long long twa_last_launch_count(const twa_handle* h);
 
+/* Diagnostic: m[i] = 1/k2[i] for n device floats, computed as the FP32 transform passes compute
+   the Poisson multiplier of Eq. mft_normed (a reciprocal approximation refined by one
+   Newton-Raphson step; 0 where k2[i] <= 0), so tests can hold that arithmetic against IEEE
+   division.  Asynchronous on `stream`.  Errors: TWA_EINVAL (null pointer, n < 0), TWA_ECUDA. */
+int twa_poisson_multiplier(const float* k2, float* m, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

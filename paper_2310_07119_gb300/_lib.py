@@ -65,6 +65,7 @@ _SIGS = {
     "twa_last_error": (ctypes.c_char_p, [_P]),
     "twa_autotune": (ctypes.c_int, [_P, _P, ctypes.c_char_p, _P]),
     "twa_last_launch_count": (ctypes.c_longlong, [_P]),
+    "twa_poisson_multiplier": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
     "twa_fno_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(FnoConfig), ctypes.c_uint64]),
     "twa_fno_destroy": (ctypes.c_int, [_P]),
     "twa_fno_num_params": (ctypes.c_longlong, [_P]),

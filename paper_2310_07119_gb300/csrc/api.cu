@@ -1329,6 +1329,14 @@ int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_m
 
 long long twa_last_launch_count(const twa_handle* h) { return h ? h->launches : 0; }
 
+int twa_poisson_multiplier(const float* k2, float* m, long long n, void* stream) {
+    twa_handle* h = nullptr;
+    if (!k2 || !m || n < 0) return fail(h, TWA_EINVAL, "twa_poisson_multiplier: bad argument");
+    launch_poisson_multiplier(k2, m, n, (cudaStream_t)stream);
+    CU(cudaGetLastError());
+    return TWA_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------

@@ -26,6 +26,8 @@ int launch_store_series(const double* cur, double* series, int* counter, int n, 
 // max over the batch of |re| and |im| of n complex values, folded into *vmax (float bits; *vmax must
 // start at 0 or at an earlier maximum)
 int launch_max_abs(const float2* buf, long long n, unsigned* vmax, cudaStream_t st);
+// m[i] = the transform passes' Poisson multiplier for k2[i]
+int launch_poisson_multiplier(const float* k2, float* m, long long n, cudaStream_t st);
 // test particles of one instance (one per slot), W the packed Poisson field in real space
 int launch_particles(const float2* W, long long cells, const int* n, int dim, double L, const double* const* ker,
                      double fscale, double kick_dt, double drift_dt, int n_slots, double* prt, cudaStream_t st);

@@ -476,6 +476,16 @@ int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, 
     k_finish_scalars<<<1, 256, 0, st>>>(part_r, nb_r, part_m, nb_m, dV, q_offset, scalars, err_word);
     return 0;
 }
+__global__ void k_poisson_multiplier(const float* __restrict__ k2, float* __restrict__ m, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m[i] = inv_k2(k2[i]);
+}
+int launch_poisson_multiplier(const float* k2, float* m, long long n, cudaStream_t st) {
+    if (n <= 0) return 0;
+    const long long b = (n + 255) / 256;
+    k_poisson_multiplier<<<(int)(b < 152 * 8 ? b : 152 * 8), 256, 0, st>>>(k2, m, n);
+    return 0;
+}
 int launch_max_abs(const float2* buf, long long n, unsigned* vmax, cudaStream_t st) {
     const long long b = (n + 255) / 256;
     k_max_abs<<<(int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8), 256, 0, st>>>(buf, n, vmax);

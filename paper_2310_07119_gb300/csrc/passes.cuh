@@ -88,6 +88,19 @@ __device__ __forceinline__ float2 kick_phase(float2 z, float theta) {
     return make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
 }
 
+// Poisson multiplier 1/k^2 (0 for the k = 0 mode) without the quotient path of an IEEE division,
+// whose per-value check and branch made the Poisson pass 20 % slower: the reciprocal approximation
+// r0 = rcp.approx(k^2) (relative error e) refined by one Newton-Raphson step for 1/x,
+// r1 = r0 + r0 (1 - k^2 r0) = (1 - e^2) / k^2 before its final rounding, so r1 is within 1 ulp of
+// 1/k^2 and correctly rounded unless 1/k^2 lies within ~e^2 of a rounding boundary.  For any grid
+// both k^2 >= (2 pi / L)^2 and 1/k^2 are normal floats, so flushing subnormals changes nothing.
+__device__ __forceinline__ float inv_k2(float k2) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(k2));
+    r = fmaf(r, fmaf(-k2, r, 1.0f), r);
+    return k2 > 0.f ? r : 0.f;
+}
+
 // z * exp(-i (k_hi + k_lo) W): the kick with its scale carried in two floats.
 __device__ __forceinline__ float2 kick_w(float2 z, float k_hi, float k_lo, float W) {
     return kick_phase(z, fmaf(k_hi, W, k_lo * W));
@@ -226,7 +239,7 @@ k_line(const PassArgs a) {
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
             const float k2 = k2f + __ldg(&a.k2a[pos_spec<N>(t, i)]);
-            const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
+            const float m = inv_k2(k2);
             w[i] = make_float2(w[i].x * m, w[i].y * m);
         }
     };
@@ -388,7 +401,7 @@ k_line(const PassArgs a) {
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) {
                 const float k2 = __ldg(&a.k2x[pos_spec<N>(t, i)]);
-                const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
+                const float m = inv_k2(k2);
                 w[i] = make_float2(w[i].x * m, w[i].y * m);
             }
             fft_line<N, true, WARP, MASK, TS>(w, t, sm, tw);
@@ -447,7 +460,7 @@ k_plane(const PassArgs a) {
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
             const float k2 = k2f + __ldg(&a.k2y[pos_spec<N>(tc, i)]);
-            const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
+            const float m = inv_k2(k2);
             w[i] = make_float2(w[i].x * m, w[i].y * m);
         }
     };

@@ -172,7 +172,7 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
 #pragma unroll
             for (int i = 0; i < RMAX; ++i) {
                 const float k2 = k2f + __ldg(&a.k2a[pos_spec<N>(t, i)]);
-                const float m = (k2 > 0.f) ? 1.0f / k2 : 0.f;
+                const float m = inv_k2(k2);
                 v[i] = make_float2(v[i].x * m, v[i].y * m);
             }
             fft_line<N, true, WARP, MASK>(v, t, sm, tw);

@@ -17,7 +17,7 @@ from . import _lib as L
 __all__ = [
     "TwaError", "twa_create", "twa_destroy", "twa_batch_elems", "twa_sample", "twa_step_batch",
     "twa_moments", "twa_run", "twa_sync_status", "twa_last_error", "twa_autotune",
-    "twa_last_launch_count", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_particles_set", "twa_particles_get", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
+    "twa_last_launch_count", "twa_poisson_multiplier", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_particles_set", "twa_particles_get", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
     "F64_PLAIN", "SCALAR_NAMES", "PASS_NAMES",
 ]
 
@@ -189,6 +189,14 @@ def twa_autotune(h, psi, cache_path: Optional[str] = None, stream=None) -> None:
 
 def twa_last_launch_count(h) -> int:
     return int(_lib().twa_last_launch_count(h))
+
+
+def twa_poisson_multiplier(k2, m=None, stream=None):
+    """The transform passes' Poisson multiplier 1/k2 (0 where k2 <= 0) of a device float32 tensor."""
+    if m is None:
+        m = torch.empty_like(k2)
+    _check(_lib().twa_poisson_multiplier(_ptr(k2), _ptr(m), int(k2.numel()), _stream(stream)), None)
+    return m
 
 
 class Ensemble:
