@@ -73,12 +73,16 @@ __device__ __forceinline__ void prefetch_l2_sector(const void* p) { asm volatile
 // their Taylor polynomials through theta^7 and theta^8 (truncation below 1e-11, so the result is
 // correctly rounded to float up to the rounding of the evaluation); otherwise theta is reduced to
 // [-pi, pi] by a two-constant (Cody-Waite) split of 2 pi and sincosf is used.
+__device__ __forceinline__ float2 kick_small(float2 z, float theta) {
+    const float t2 = theta * theta;
+    const float s = theta * fmaf(t2, fmaf(t2, fmaf(t2, -1.9841269841e-4f, 8.3333333333e-3f), -1.6666666667e-1f), 1.0f);
+    const float c = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 2.4801587302e-5f, -1.3888888889e-3f), 4.1666666667e-2f), -0.5f), 1.0f);
+    return make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
+}
 __device__ __forceinline__ float2 kick_phase(float2 z, float theta) {
     float s, c;
     if (fabsf(theta) <= 0.25f) {
-        const float t2 = theta * theta;
-        s = theta * fmaf(t2, fmaf(t2, fmaf(t2, -1.9841269841e-4f, 8.3333333333e-3f), -1.6666666667e-1f), 1.0f);
-        c = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 2.4801587302e-5f, -1.3888888889e-3f), 4.1666666667e-2f), -0.5f), 1.0f);
+        return kick_small(z, theta);
     } else {
         const float n = rintf(theta * 0.15915494309189535f);
         float r = fmaf(-n, 6.28125f, theta);
@@ -104,6 +108,27 @@ __device__ __forceinline__ float inv_k2(float k2) {
 // z * exp(-i (k_hi + k_lo) W): the kick with its scale carried in two floats.
 __device__ __forceinline__ float2 kick_w(float2 z, float k_hi, float k_lo, float W) {
     return kick_phase(z, fmaf(k_hi, W, k_lo * W));
+}
+
+// The kick of a thread's R values, W_i = W(i), with one branch per thread instead of one per value:
+// the Taylor form for all when every |theta_i| <= 1/4, else kick_phase for all.
+template <int R, class G>
+__device__ __forceinline__ void kick_all(float2 (&v)[R], float k_hi, float k_lo, G W_of) {
+    float th[R];
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const float W = W_of(i);
+        th[i] = fmaf(k_hi, W, k_lo * W);
+        m = fmaxf(m, fabsf(th[i]));
+    }
+    if (m <= 0.25f) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = kick_small(v[i], th[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = kick_phase(v[i], th[i]);
+    }
 }
 
 // At least 512 resident threads (16 warps) per SM so that one CTA's loads overlap another's
@@ -275,8 +300,7 @@ k_line(const PassArgs a) {
             load_nat(v, F);
             if (kick) {
                 const float* sv = stv + h * RMAX * NTH;
-#pragma unroll
-                for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, sv[i * NTH]);
+                kick_all(v, a.kick, a.kick_lo, [&](int i) { return sv[i * NTH]; });
             }
             if constexpr (OP == OP_KICK_DRIFT) {
                 drift(v);
@@ -305,8 +329,7 @@ k_line(const PassArgs a) {
             float2* F = a.psi + (long long)slot * a.cells;
             load_nat(v, F);
             const float* sv = stv + h * RMAX * NTH;
-#pragma unroll
-            for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, sv[i * NTH]);
+            kick_all(v, a.kick, a.kick_lo, [&](int i) { return sv[i * NTH]; });
             if constexpr (OP == OP_KICK_DRIFT_VINV) drift(v);
             store_nat(v, F);
         }
@@ -387,11 +410,8 @@ k_line(const PassArgs a) {
         for (int st = 0; st < a.nsteps; ++st) {
             const float kk = (st == 0) ? a.kick : a.kick2;
             const float kl = (st == 0) ? a.kick_lo : a.kick2_lo;
-#pragma unroll
-            for (int i = 0; i < RMAX; ++i) {
-                v[i] = kick_w(v[i], kk, kl, w[i].x);
-                u1[i] = kick_w(u1[i], kk, kl, w[i].y);
-            }
+            kick_all(v, kk, kl, [&](int i) { return w[i].x; });
+            kick_all(u1, kk, kl, [&](int i) { return w[i].y; });
             drift(v);
             drift(u1);
 #pragma unroll
@@ -483,8 +503,7 @@ k_plane(const PassArgs a) {
                 for (int i = 0; i < RMAX; ++i) v[i] = __ldcg(&F[row + pos_nat<N>(tr, i)]);
 #pragma unroll
                 for (int i = 0; i < RMAX; ++i) w[i] = __ldcg(&Wh[2 * (row + pos_nat<N>(tr, i))]);
-#pragma unroll
-                for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, w[i]);
+                kick_all(v, a.kick, a.kick_lo, [&](int i) { return w[i]; });
                 fft_line<N, false, WARP, MASK>(v, tr, smr, tw);
                 phase(v, a.ph, tr);
                 fft_line<N, true, WARP, MASK>(v, tr, smr, tw);

@@ -216,8 +216,7 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
                 if (slot < a.n_slots) {
                     ld(false);
                     const float* sv = reinterpret_cast<const float*>(psm + 2 * SE) + threadIdx.x + (sub - 1) * RMAX * NTH;
-#pragma unroll
-                    for (int i = 0; i < RMAX; ++i) v[i] = kick_w(v[i], a.kick, a.kick_lo, sv[i * NTH]);
+                    kick_all(v, a.kick, a.kick_lo, [&](int i) { return sv[i * NTH]; });
                     drift();
                     st_nat(a.psi + (long long)slot * a.cells);
                 }
