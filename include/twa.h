@@ -285,6 +285,38 @@ int twa_autotune(twa_handle* h, void* psi, const char* cache_path, void* stream)
 /* Number of kernel launches the last twa_step_batch / twa_run / twa_moments call enqueued. */
 long long twa_last_launch_count(const twa_handle* h);
 
+/* Stream averages of user functions (Appendix B: the synthesizer that evaluates arbitrary
+   functions of the streams' fields and averages them across the streams, applied to every
+   stream before averaging or to the averaged field).  f = f_re + i f_im is given as two C
+   expressions (f_im NULL or "" means 0) in the double variables re, im (the field value), the
+   long long i (index of the cell or mode, x fastest) and n (cells), and the ints nx, ny, nz;
+   the CUDA math functions (sqrt, exp, atan2, pow, ...) are available.  Expressions are limited
+   to arithmetic: brackets, braces, ';', '#', quotes, "->", "__" and pointer casts are refused.
+   twa_observable_create compiles f with NVRTC (libnvrtc, opened on first use) for the current
+   device.  Errors: TWA_EINVAL (bad flags, a refused or non-compiling expression; the compiler log
+   is in twa_last_error(NULL)), TWA_ECUDA (no NVRTC or device).  flags: */
+#define TWA_OBS_OF_MEAN 1  /* f of the streams' mean field, not the mean of f over the streams */
+#define TWA_OBS_MODES   2  /* f of the Fourier amplitudes a_k = sqrt(n_tot dV / cells) DFT(psi)_k
+                              (the number-unit amplitudes of the mode moments; FP32 path with
+                              want_modes) instead of the field psi(x) */
+typedef struct twa_observable twa_observable;
+int twa_observable_create(twa_observable** out, const char* f_re, const char* f_im, int flags);
+
+/* Evaluate on instance `inst` of a synchronized batch psi, asynchronously on `stream`.  Over the
+   sampled streams s = 1..n_real, per cell (or mode) c: per_cell[c] = (1/n_real) sum_s f(psi_s(c))
+   or, with TWA_OBS_OF_MEAN, f((1/n_real) sum_s psi_s(c)); f_cl[c] = f(psi_0(c)) of the classical
+   slot; total = sum_c per_cell[c] dV (position space) or sum_c per_cell[c] (modes).  per_cell and
+   f_cl (device, 2 * cells doubles, complex interleaved) may be NULL; total (device, 2 doubles) may
+   not.  Streams are summed in slot order and the total in a fixed order, so results are
+   reproducible.  The evaluation is in FP64 (GB300's FP64 rate is 1/64 of FP32: expensive
+   functions of 10^8-10^9 stream values take milliseconds to tens of milliseconds).  With
+   TWA_OBS_MODES the handle's spectral scratch is overwritten.  Errors: TWA_EINVAL, TWA_ECUDA. */
+int twa_observable_eval(twa_observable* ob, twa_handle* h, int inst, const void* psi, double* per_cell,
+                        double* f_cl, double* total, void* stream);
+
+/* Release an observable (accepts NULL). */
+int twa_observable_destroy(twa_observable* ob);
+
 /* Diagnostic: m[i] = 1/k2[i] for n device floats, computed as the FP32 transform passes compute
    the Poisson multiplier of Eq. mft_normed (a reciprocal approximation refined by one
    Newton-Raphson step; 0 where k2[i] <= 0), so tests can hold that arithmetic against IEEE

@@ -142,6 +142,45 @@ def phase_moments(batch: np.ndarray, n_tot: float, L: float, dim: int) -> dict:
             "var_a": float(np.sum(wa) * dV), "var_phi": float(np.sum(rho * phi2) * dV / (math.pi ** 2 / 3.0))}
 
 
+def stream_average(batch: np.ndarray, f, n_tot: float, L: float, dim: int, of_mean: bool = False,
+                   modes: bool = False) -> dict:
+    """Average of a function of the fields across the streams (Appendix B's synthesizer).
+
+    f(re, im, i, n) takes the real and imaginary parts of the field value, the flat index i of
+    the cell or mode (C order of ``batch[s]``, x fastest) and the number of cells n, elementwise
+    on arrays, and returns a complex (or real) array.  Over the sampled slots s = 1..N_s:
+        per_cell = mean_s f(psi_s)            (of_mean False: f applied to every stream)
+        per_cell = f(mean_s psi_s)            (of_mean True: f applied to the averaged field)
+        f_cl     = f(psi_0)                   (the classical slot)
+        total    = sum over cells of per_cell dV
+    With modes, the field is replaced by the number-unit Fourier amplitudes
+    a_k = sqrt(n_tot dV / cells) DFT(psi)_k of each slot (as in ``moments``) and the total is the
+    plain sum over modes.
+    """
+    shape = batch.shape[1:]
+    cells = batch[0].size
+    dV = (L ** dim) / cells
+    fields = batch.reshape(batch.shape[0], cells)
+    w = dV
+    if modes:
+        fields = np.sqrt(n_tot * dV / cells) * sp.fftn(batch, dim).reshape(batch.shape[0], cells)
+        w = 1.0
+    idx = np.arange(cells, dtype=np.int64)
+
+    def g(z):
+        return np.asarray(f(z.real, z.imag, idx, cells), dtype=np.complex128) * np.ones(cells)
+
+    if of_mean:
+        per_cell = g(fields[1:].mean(0))
+    else:
+        per_cell = np.zeros(cells, dtype=np.complex128)
+        for s in range(1, fields.shape[0]):
+            per_cell += g(fields[s])
+        per_cell /= fields.shape[0] - 1
+    return {"per_cell": per_cell.reshape(shape), "f_cl": g(fields[0]).reshape(shape),
+            "total": complex(per_cell.sum() * w)}
+
+
 def adaptive_dt(batch: np.ndarray, hbar: float, C: float, L: float, dim: int, c_f: float) -> float:
     """Time step of Sec. III.B.2 (the dynamic Delta t rule), read in normalized units:
 

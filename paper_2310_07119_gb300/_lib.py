@@ -15,6 +15,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "twa.h")
 TWA_OK, TWA_EINVAL, TWA_ENOMEM, TWA_ECUDA, TWA_ETIMEOUT, TWA_ENONFINITE = 0, -1, -2, -3, -4, -5
 TWA_F32, TWA_F64_PLAIN = 0, 1
 TWA_NSCALARS = 8
+TWA_OBS_OF_MEAN, TWA_OBS_MODES = 1, 2
 SCALAR_NAMES = ("Q", "corr", "mass", "mass_cl", "nonfinite", "nk_sum", "drho_l2", "rhocl_l2")
 # Pass kinds of the FP32 pipelines, in the library's numbering (profiler ops).
 PASS_NAMES = ("drift", "kick_drift", "kick_drift_vinv", "drift_rho", "rho_fwd", "fwd", "fwd_mul_inv", "inv",
@@ -66,6 +67,9 @@ _SIGS = {
     "twa_autotune": (ctypes.c_int, [_P, _P, ctypes.c_char_p, _P]),
     "twa_last_launch_count": (ctypes.c_longlong, [_P]),
     "twa_poisson_multiplier": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
+    "twa_observable_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int]),
+    "twa_observable_eval": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "twa_observable_destroy": (ctypes.c_int, [_P]),
     "twa_fno_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(FnoConfig), ctypes.c_uint64]),
     "twa_fno_destroy": (ctypes.c_int, [_P]),
     "twa_fno_num_params": (ctypes.c_longlong, [_P]),

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "observable.h"
 #include "passes.cuh"
 #include "pipe.cuh"
 #include "twa.h"
@@ -1266,6 +1267,83 @@ const char* twa_last_error(const twa_handle* h) { return h ? h->err.c_str() : g_
 
 // Record a failure of a handle-free entry point, reported by twa_last_error(NULL).
 void twa_set_global_error(const std::string& msg) { g_create_error = msg; }
+
+// ---------------------------------------------------------------------------------------------
+// Stream averages of user functions (Appendix B's synthesizer), compiled at run time.
+struct twa_observable {
+    twa::ObsProgram* prog = nullptr;
+    int flags = 0;
+    double* part = nullptr;  // per-block partial sums, allocated on the first evaluation
+};
+
+namespace {
+constexpr int kObsBlocks = 152 * 8;
+}
+
+extern "C" {
+
+int twa_observable_create(twa_observable** out, const char* f_re, const char* f_im, int flags) {
+    if (!out || !f_re || (flags & ~(TWA_OBS_OF_MEAN | TWA_OBS_MODES)))
+        return fail(nullptr, TWA_EINVAL, "twa_observable_create: bad argument");
+    *out = nullptr;
+    std::string msg;
+    twa::ObsProgram* prog = nullptr;
+    const int rc = twa::obs_compile(f_re, f_im, &prog, &msg);
+    if (rc) return fail(nullptr, rc == -1 ? TWA_EINVAL : TWA_ECUDA, msg);
+    twa_observable* ob = new twa_observable();
+    ob->prog = prog;
+    ob->flags = flags;
+    *out = ob;
+    return TWA_OK;
+}
+
+int twa_observable_destroy(twa_observable* ob) {
+    if (!ob) return TWA_OK;
+    if (ob->part) cudaFree(ob->part);
+    twa::obs_free(ob->prog);
+    delete ob;
+    return TWA_OK;
+}
+
+int twa_observable_eval(twa_observable* ob, twa_handle* h, int inst, const void* psi, double* per_cell, double* f_cl,
+                        double* total, void* stream) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!ob || !psi || !total || inst < 0 || inst >= (int)h->in.size())
+        return fail(h, TWA_EINVAL, "twa_observable_eval: bad argument");
+    if (misaligned(psi)) return fail(h, TWA_EINVAL, "twa_observable_eval: psi must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    h->launches = 0;
+    Inst& I = h->in[inst];
+    if (!ob->part) CU(cudaMalloc(&ob->part, sizeof(double) * 2 * kObsBlocks));
+    const void* src = nullptr;
+    double scale = 1.0, w = I.dV;
+    bool f64 = false;
+    if (ob->flags & TWA_OBS_MODES) {
+        if (h->p.precision != TWA_F32 || !I.spec)
+            return fail(h, TWA_EINVAL, "twa_observable_eval: Fourier amplitudes need the FP32 path and want_modes");
+        // a_k = sqrt(n_tot dV / cells) DFT(psi)_k for every slot, as the moments form them
+        float2* f = inst_psi(I, const_cast<void*>(psi));
+        RC(run_pass(h, I, f, 0, OP_KICK_FWD_OUT, 0.0, I.vc, I.spec, I.n_pairs, st, 0, I.mode == MODE_1D ? 1 : 0));
+        for (int ax = 1; ax < I.dim; ++ax) RC(run_pass(h, I, f, ax, OP_FWD, 0.0, I.spec, nullptr, I.n_slots, st));
+        h->launches += I.dim;
+        src = I.spec;
+        scale = std::sqrt(h->p.n_tot * I.dV / (double)I.cells);
+        w = 1.0;
+    } else if (h->p.precision == TWA_F32) {
+        src = inst_psi(I, const_cast<void*>(psi));
+    } else {
+        src = static_cast<const double2*>(psi) + I.off;
+        f64 = true;
+    }
+    std::string msg;
+    if (twa::obs_launch(ob->prog, f64, src, I.cells, I.n_slots, (ob->flags & TWA_OBS_OF_MEAN) ? 1 : 0, scale, I.n,
+                        per_cell, f_cl, ob->part, kObsBlocks, w, total, st, &msg))
+        return fail(h, TWA_ECUDA, msg);
+    h->launches += 2;
+    return TWA_OK;
+}
+
+}  // extern "C"
 
 extern "C" {
 

@@ -17,7 +17,8 @@ from . import _lib as L
 __all__ = [
     "TwaError", "twa_create", "twa_destroy", "twa_batch_elems", "twa_sample", "twa_step_batch",
     "twa_moments", "twa_run", "twa_sync_status", "twa_last_error", "twa_autotune",
-    "twa_last_launch_count", "twa_poisson_multiplier", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_particles_set", "twa_particles_get", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
+    "twa_last_launch_count", "twa_poisson_multiplier", "twa_observable_create", "twa_observable_eval",
+    "twa_observable_destroy", "Observable", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_particles_set", "twa_particles_get", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
     "F64_PLAIN", "SCALAR_NAMES", "PASS_NAMES",
 ]
 
@@ -189,6 +190,64 @@ def twa_autotune(h, psi, cache_path: Optional[str] = None, stream=None) -> None:
 
 def twa_last_launch_count(h) -> int:
     return int(_lib().twa_last_launch_count(h))
+
+
+def twa_observable_create(f_re: str, f_im: Optional[str] = None, flags: int = 0):
+    """Compile f = f_re + i f_im (C expressions in re, im, i, n, nx, ny, nz) into a stream average."""
+    ob = ctypes.c_void_p()
+    _check(_lib().twa_observable_create(ctypes.byref(ob), f_re.encode(), f_im.encode() if f_im else None,
+                                        int(flags)), None)
+    return ob
+
+
+def twa_observable_eval(ob, h, inst: int, psi, per_cell=None, f_cl=None, total=None, stream=None):
+    """Evaluate on one instance; per_cell / f_cl are complex128 device tensors (one value per cell or
+    mode) or None; returns the device float64 tensor `total` (real, imaginary)."""
+    if total is None:
+        total = torch.zeros(2, dtype=torch.float64, device=psi.device)
+    _check(_lib().twa_observable_eval(ob, h, int(inst), _ptr(psi), _ptr(per_cell), _ptr(f_cl), _ptr(total),
+                                      _stream(stream)), h)
+    return total
+
+
+def twa_observable_destroy(ob) -> None:
+    _check(_lib().twa_observable_destroy(ob), None)
+
+
+class Observable:
+    """A compiled stream average of f (Appendix B's synthesizer); see twa_observable_create.
+
+    of_mean: apply f to the streams' mean field instead of averaging f over the streams.
+    modes: apply f to the Fourier amplitudes a_k (number units) instead of psi(x).
+    """
+
+    def __init__(self, f_re: str, f_im: Optional[str] = None, of_mean: bool = False, modes: bool = False):
+        flags = (L.TWA_OBS_OF_MEAN if of_mean else 0) | (L.TWA_OBS_MODES if modes else 0)
+        self.ob = twa_observable_create(f_re, f_im, flags)
+
+    def __call__(self, ens: "Ensemble", inst: int = 0, psi=None, per_cell: bool = True, classical: bool = False,
+                 stream=None) -> dict:
+        """Evaluate on instance `inst` of an Ensemble's batch (or of `psi`): a dict with the complex
+        per-cell (or per-mode) average 'per_cell', f of the classical slot 'f_cl' (if asked) and the
+        complex 'total'."""
+        psi = ens.psi if psi is None else psi
+        cells = ens.cells[inst]
+        pc = torch.empty(cells, dtype=torch.complex128, device=psi.device) if per_cell else None
+        fc = torch.empty(cells, dtype=torch.complex128, device=psi.device) if classical else None
+        tot = twa_observable_eval(self.ob, ens.h, inst, psi, pc, fc, None, stream)
+        t = tot.cpu().numpy()
+        return {"per_cell": pc, "f_cl": fc, "total": complex(t[0], t[1])}
+
+    def close(self) -> None:
+        if self.ob is not None:
+            twa_observable_destroy(self.ob)
+            self.ob = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def twa_poisson_multiplier(k2, m=None, stream=None):

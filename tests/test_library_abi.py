@@ -47,3 +47,25 @@ def test_python_binding_has_no_cpu_path():
     from paper_2310_07119_gb300 import TwaError, twa_create
     with pytest.raises(TwaError):
         twa_create([(1, (64,), 1.0)], 1.0, 1.0, 1e-3, 1e4, [4])
+
+
+@pytest.mark.parametrize("expr", ["", "re[0]", "re; im", "{re}", "#define x", "\"a\"", "*(double*)0", "p->x",
+                                  "__ldg(0)", "asm(\"\")", "re // c"])
+def test_observable_refuses_expressions_outside_arithmetic(lib, expr):
+    ob = ctypes.c_void_p()
+    rc = lib.twa_observable_create(ctypes.byref(ob), expr.encode(), None, 0)
+    assert rc == _lib.TWA_EINVAL and not ob.value
+    assert b"twa_observable_create" in lib.twa_last_error(None)
+
+
+def test_observable_rejects_unknown_flags(lib):
+    ob = ctypes.c_void_p()
+    assert lib.twa_observable_create(ctypes.byref(ob), b"re", None, 4) == _lib.TWA_EINVAL
+    assert lib.twa_observable_destroy(None) == _lib.TWA_OK
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device error path")
+def test_observable_without_a_device_fails_loudly(lib):
+    ob = ctypes.c_void_p()
+    rc = lib.twa_observable_create(ctypes.byref(ob), b"re*re + im*im", None, 0)
+    assert rc == _lib.TWA_ECUDA and not ob.value
