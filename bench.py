@@ -266,6 +266,30 @@ def _phase_moments_cost(ens, w, reps=3):
     return {"ms_per_call": ms, "GBps": nbytes / (ms * 1e-3) / 1e9, "var_a": float(tot[0]), "var_phi": float(tot[1])}
 
 
+def _observable_cost(ens, w, reps=3):
+    """Stream averages of user functions (Appendix B's synthesizer) on the bench batch: one read of
+    every stream per call, f evaluated and summed in FP64.  A polynomial and a transcendental f."""
+    import torch
+    from paper_2310_07119_gb300 import Observable
+    out = {}
+    nbytes = (STREAMS + 1) * w.grid.cells * 8
+    for name, (fre, fim) in {"density": ("re*re + im*im", None),
+                             "phase_and_amplitude": ("atan2(im, re)", "sqrt(re*re + im*im)")}.items():
+        ob = Observable(fre, fim)
+        r = ob(ens)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ob(ens)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_call": ms, "GBps": nbytes / (ms * 1e-3) / 1e9, "total_re": r["total"].real}
+        ob.close()
+    return out
+
+
 def _particles_rate(ens, w, n_out=3):
     """The bench batch advanced with one test particle per stream (Sec. III.D): the particle update
     runs before every step, with the Poisson field brought to real space where the pipeline keeps
@@ -474,6 +498,7 @@ def run_twa(args):
         line["e2e"] = _e2e(ens, w)
         line["adaptive"] = _adaptive_rate(ens, w)
         line["phase_moments"] = _phase_moments_cost(ens, w)
+        line["observable"] = _observable_cost(ens, w)
         line["particles"] = _particles_rate(ens, w)
         ens.close()
         torch.cuda.empty_cache()
