@@ -310,7 +310,8 @@ int twa_observable_create(twa_observable** out, const char* f_re, const char* f_
    not.  Streams are summed in slot order and the total in a fixed order, so results are
    reproducible.  The evaluation is in FP64 (GB300's FP64 rate is 1/64 of FP32: expensive
    functions of 10^8-10^9 stream values take milliseconds to tens of milliseconds).  With
-   TWA_OBS_MODES the handle's spectral scratch is overwritten.  Errors: TWA_EINVAL, TWA_ECUDA. */
+   TWA_OBS_MODES the handle's spectral scratch is overwritten.  An observable keeps one buffer of
+   partial sums: evaluate it on one stream at a time.  Errors: TWA_EINVAL, TWA_ECUDA. */
 int twa_observable_eval(twa_observable* ob, twa_handle* h, int inst, const void* psi, double* per_cell,
                         double* f_cl, double* total, void* stream);
 

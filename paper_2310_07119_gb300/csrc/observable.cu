@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -125,6 +126,8 @@ struct Nvrtc {
 
 Nvrtc& nvrtc() {
     static Nvrtc n;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     if (n.tried) return n;
     n.tried = true;
     for (const char* name : {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
