@@ -268,14 +268,17 @@ def _phase_moments_cost(ens, w, reps=3):
 
 def _observable_cost(ens, w, reps=3):
     """Stream averages of user functions (Appendix B's synthesizer) on the bench batch: one read of
-    every stream per call, f evaluated and summed in FP64.  A polynomial and a transcendental f."""
+    every stream per call, f evaluated and summed in FP64, or in FP32 with float-pair sums.  A
+    polynomial and a transcendental f."""
     import torch
     from paper_2310_07119_gb300 import Observable
     out = {}
     nbytes = (STREAMS + 1) * w.grid.cells * 8
-    for name, (fre, fim) in {"density": ("re*re + im*im", None),
-                             "phase_and_amplitude": ("atan2(im, re)", "sqrt(re*re + im*im)")}.items():
-        ob = Observable(fre, fim)
+    for name, (fre, fim, fp32) in {"density": ("re*re + im*im", None, False),
+                                   "phase_and_amplitude": ("atan2(im, re)", "sqrt(re*re + im*im)", False),
+                                   "density_fp32": ("re*re + im*im", None, True),
+                                   "phase_and_amplitude_fp32": ("atan2(im, re)", "sqrt(re*re + im*im)", True)}.items():
+        ob = Observable(fre, fim, fp32=fp32)
         r = ob(ens)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

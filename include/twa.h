@@ -299,6 +299,10 @@ long long twa_last_launch_count(const twa_handle* h);
 #define TWA_OBS_MODES   2  /* f of the Fourier amplitudes a_k = sqrt(n_tot dV / cells) DFT(psi)_k
                               (the number-unit amplitudes of the mode moments; FP32 path with
                               want_modes) instead of the field psi(x) */
+#define TWA_OBS_FP32    4  /* evaluate f in FP32 (re, im float) and sum over the streams as float
+                              pairs: about 1e-7 relative per value, much faster than FP64; math
+                              functions then take float arguments (pow(x, 2.0f), not 2.0, which
+                              is an ambiguous overload the compiler log reports) */
 typedef struct twa_observable twa_observable;
 int twa_observable_create(twa_observable** out, const char* f_re, const char* f_im, int flags);
 

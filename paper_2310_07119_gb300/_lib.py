@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "twa.h")
 TWA_OK, TWA_EINVAL, TWA_ENOMEM, TWA_ECUDA, TWA_ETIMEOUT, TWA_ENONFINITE = 0, -1, -2, -3, -4, -5
 TWA_F32, TWA_F64_PLAIN = 0, 1
 TWA_NSCALARS = 8
-TWA_OBS_OF_MEAN, TWA_OBS_MODES = 1, 2
+TWA_OBS_OF_MEAN, TWA_OBS_MODES, TWA_OBS_FP32 = 1, 2, 4
 SCALAR_NAMES = ("Q", "corr", "mass", "mass_cl", "nonfinite", "nk_sum", "drho_l2", "rhocl_l2")
 # Pass kinds of the FP32 pipelines, in the library's numbering (profiler ops).
 PASS_NAMES = ("drift", "kick_drift", "kick_drift_vinv", "drift_rho", "rho_fwd", "fwd", "fwd_mul_inv", "inv",

@@ -1283,12 +1283,12 @@ constexpr int kObsBlocks = 152 * 8;
 extern "C" {
 
 int twa_observable_create(twa_observable** out, const char* f_re, const char* f_im, int flags) {
-    if (!out || !f_re || (flags & ~(TWA_OBS_OF_MEAN | TWA_OBS_MODES)))
+    if (!out || !f_re || (flags & ~(TWA_OBS_OF_MEAN | TWA_OBS_MODES | TWA_OBS_FP32)))
         return fail(nullptr, TWA_EINVAL, "twa_observable_create: bad argument");
     *out = nullptr;
     std::string msg;
     twa::ObsProgram* prog = nullptr;
-    const int rc = twa::obs_compile(f_re, f_im, &prog, &msg);
+    const int rc = twa::obs_compile(f_re, f_im, (flags & TWA_OBS_FP32) != 0, &prog, &msg);
     if (rc) return fail(nullptr, rc == -1 ? TWA_EINVAL : TWA_ECUDA, msg);
     twa_observable* ob = new twa_observable();
     ob->prog = prog;

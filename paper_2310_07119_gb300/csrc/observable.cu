@@ -3,7 +3,8 @@
 // applied either to each stream before averaging or to the averaged field).
 //
 // The user gives f as two C expressions (real and imaginary part) in the variables re, im (the
-// field value, double), i (index of the cell or mode, x fastest), n (cells) and nx, ny, nz.  The
+// field value: double, or float in the FP32 mode), i (index of the cell or mode, x fastest), n
+// (cells) and nx, ny, nz.  The
 // expressions are pasted into a fixed kernel source, compiled with NVRTC for the current device and
 // loaded as a CUDA library.  One kernel pass reads every slot of the instance once: per cell it sums
 // f over the sampled streams in slot order (or sums the field and applies f to the mean), writes the
@@ -26,12 +27,28 @@ namespace twa {
 namespace {
 
 const char* kSource = R"SRC(
-struct twa_c2 { double x, y; };
-__device__ __forceinline__ twa_c2 twa_f(double re, double im, long long i, long long n, int nx, int ny, int nz) {
+#ifdef TWA_EVAL_FP32
+// f in float; the sums over the streams as float pairs (Knuth's two-sum, the rounding errors summed)
+typedef float twa_real;
+struct twa_acc { float hi, lo; };
+__device__ __forceinline__ void twa_acc_add(twa_acc& a, float b) {
+    const float s = a.hi + b, bb = s - a.hi;
+    a.lo += (a.hi - (s - bb)) + (b - bb);
+    a.hi = s;
+}
+__device__ __forceinline__ double twa_acc_value(const twa_acc& a) { return (double)a.hi + (double)a.lo; }
+#else
+typedef double twa_real;
+struct twa_acc { double hi, lo; };
+__device__ __forceinline__ void twa_acc_add(twa_acc& a, double b) { a.hi += b; }
+__device__ __forceinline__ double twa_acc_value(const twa_acc& a) { return a.hi; }
+#endif
+struct twa_c2 { twa_real x, y; };
+__device__ __forceinline__ twa_c2 twa_f(twa_real re, twa_real im, long long i, long long n, int nx, int ny, int nz) {
     (void)re; (void)im; (void)i; (void)n; (void)nx; (void)ny; (void)nz;
     twa_c2 r;
-    r.x = (double)(TWA_F_RE);
-    r.y = (double)(TWA_F_IM);
+    r.x = (twa_real)(TWA_F_RE);
+    r.y = (twa_real)(TWA_F_IM);
     return r;
 }
 template <class T2>
@@ -40,41 +57,44 @@ __device__ __forceinline__ void twa_obs_body(const T2* __restrict__ psi, long lo
                                              double2* __restrict__ cl, double* __restrict__ part) {
     __shared__ double sr[256], si[256];
     const double inv_ns = 1.0 / (double)(n_slots - 1);
+    const twa_real sc = (twa_real)scale;
     double tr = 0.0, ti = 0.0;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
          c += (long long)gridDim.x * blockDim.x) {
-        double ar = 0.0, ai = 0.0;
+        twa_acc ar = {0, 0}, ai = {0, 0};
+        double vr, vi;
         if (of_mean) {
             for (int s = 1; s < n_slots; ++s) {
                 const T2 z = psi[(long long)s * cells + c];
-                ar += (double)z.x;
-                ai += (double)z.y;
+                twa_acc_add(ar, (twa_real)z.x);
+                twa_acc_add(ai, (twa_real)z.y);
             }
-            const twa_c2 v = twa_f(ar * inv_ns * scale, ai * inv_ns * scale, c, cells, nx, ny, nz);
-            ar = v.x;
-            ai = v.y;
+            const twa_c2 v = twa_f((twa_real)(twa_acc_value(ar) * inv_ns * scale),
+                                   (twa_real)(twa_acc_value(ai) * inv_ns * scale), c, cells, nx, ny, nz);
+            vr = (double)v.x;
+            vi = (double)v.y;
         } else {
             for (int s = 1; s < n_slots; ++s) {
                 const T2 z = psi[(long long)s * cells + c];
-                const twa_c2 v = twa_f((double)z.x * scale, (double)z.y * scale, c, cells, nx, ny, nz);
-                ar += v.x;
-                ai += v.y;
+                const twa_c2 v = twa_f((twa_real)z.x * sc, (twa_real)z.y * sc, c, cells, nx, ny, nz);
+                twa_acc_add(ar, v.x);
+                twa_acc_add(ai, v.y);
             }
-            ar *= inv_ns;
-            ai *= inv_ns;
+            vr = twa_acc_value(ar) * inv_ns;
+            vi = twa_acc_value(ai) * inv_ns;
         }
         if (out) {
-            out[c].x = ar;
-            out[c].y = ai;
+            out[c].x = vr;
+            out[c].y = vi;
         }
         if (cl) {
             const T2 z = psi[c];
-            const twa_c2 v = twa_f((double)z.x * scale, (double)z.y * scale, c, cells, nx, ny, nz);
-            cl[c].x = v.x;
-            cl[c].y = v.y;
+            const twa_c2 v = twa_f((twa_real)z.x * sc, (twa_real)z.y * sc, c, cells, nx, ny, nz);
+            cl[c].x = (double)v.x;
+            cl[c].y = (double)v.y;
         }
-        tr += ar;
-        ti += ai;
+        tr += vr;
+        ti += vi;
     }
     sr[threadIdx.x] = tr;
     si[threadIdx.x] = ti;
@@ -177,7 +197,7 @@ struct ObsProgram {
     cudaKernel_t k32 = nullptr, k64 = nullptr, kfin = nullptr;
 };
 
-int obs_compile(const char* f_re, const char* f_im, ObsProgram** out, std::string* msg) {
+int obs_compile(const char* f_re, const char* f_im, bool fp32, ObsProgram** out, std::string* msg) {
     *out = nullptr;
     const std::string re = f_re ? f_re : "", im = (f_im && *f_im) ? f_im : "0";
     std::string why;
@@ -197,7 +217,8 @@ int obs_compile(const char* f_re, const char* f_im, ObsProgram** out, std::strin
         *msg = "twa_observable_create: no CUDA device";
         return -3;
     }
-    const std::string src = "#define TWA_F_RE (" + re + ")\n#define TWA_F_IM (" + im + ")\n" + kSource;
+    const std::string src = std::string(fp32 ? "#define TWA_EVAL_FP32 1\n" : "") + "#define TWA_F_RE (" + re +
+                            ")\n#define TWA_F_IM (" + im + ")\n" + kSource;
     const std::string arch = "--gpu-architecture=sm_" + std::to_string(major) + std::to_string(minor);
     const char* opts[] = {arch.c_str(), "--std=c++17", "--device-as-default-execution-space"};
     nvrtcProgram prog = nullptr;

@@ -8,9 +8,10 @@ namespace twa {
 
 struct ObsProgram;
 
-// Compiles f = f_re + i f_im for the current device.  Returns 0, -1 (the expression is rejected or
-// does not compile; msg holds the reason or the compiler log) or -3 (NVRTC or CUDA unavailable).
-int obs_compile(const char* f_re, const char* f_im, ObsProgram** out, std::string* msg);
+// Compiles f = f_re + i f_im for the current device, evaluated in FP64 (sums in FP64) or, with
+// fp32, in FP32 (sums over the streams as float pairs).  Returns 0, -1 (the expression is rejected
+// or does not compile; msg holds the reason or the compiler log) or -3 (NVRTC or CUDA unavailable).
+int obs_compile(const char* f_re, const char* f_im, bool fp32, ObsProgram** out, std::string* msg);
 void obs_free(ObsProgram* p);
 
 // One averaging pass over an instance (slot 0 classical, slots 1.. sampled; values scaled by

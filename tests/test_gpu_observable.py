@@ -95,6 +95,26 @@ def test_mode_space_average_matches_the_oracle(dim, m, name):
     ens.close()
 
 
+@pytest.mark.parametrize("name", ["density", "field", "angle_abs"])
+@pytest.mark.parametrize("of_mean", [False, True])
+def test_fp32_evaluation_matches_the_oracle_to_float_rounding(name, of_mean):
+    w, ens, batch = _evolved(3, 16, 6)
+    fre, fim, _ = FUNCS[name]
+    ob = Observable(fre, fim, of_mean=of_mean, fp32=True)
+    got = ob(ens, classical=True)
+    ref = twa.stream_average(batch, _oracle_f(name, 16), w.phys.n_tot, w.grid.L, 3, of_mean=of_mean)
+    _check(got, ref, 2e-6)
+    ob.close()
+    ens.close()
+
+
+def test_fp32_evaluation_reports_an_ambiguous_overload():
+    with pytest.raises(TwaError) as e:
+        Observable("pow(re*re + im*im, 2.0)", fp32=True)
+    assert e.value.code == L.TWA_EINVAL and "pow" in str(e.value)
+    Observable("pow(re*re + im*im, 2.0f)", fp32=True).close()
+
+
 def test_fp64_plain_batch():
     w, ens, batch = _evolved(3, 16, 3, precision=1, steps=2)
     ob = Observable("re*re + im*im", "atan2(im, re)")

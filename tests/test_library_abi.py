@@ -60,7 +60,7 @@ def test_observable_refuses_expressions_outside_arithmetic(lib, expr):
 
 def test_observable_rejects_unknown_flags(lib):
     ob = ctypes.c_void_p()
-    assert lib.twa_observable_create(ctypes.byref(ob), b"re", None, 4) == _lib.TWA_EINVAL
+    assert lib.twa_observable_create(ctypes.byref(ob), b"re", None, 8) == _lib.TWA_EINVAL
     assert lib.twa_observable_destroy(None) == _lib.TWA_OK
 
 
