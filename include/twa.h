@@ -218,9 +218,11 @@ int twa_profile_read(twa_handle* h, int op, long long* launches, double* total_m
    that loads the library until the process exits.  The first call on a device looks up the device
    addresses of those arrays (make that first call before any stream capture).  Every call
    rebuilds the tables and the Poisson field; calls whose work overlaps on the GPU share the arrays
-   and race.  Errors: TWA_EINVAL when grid->dim != 1, precision != TWA_F32, n[0] is not a power of
-   two in [8, 2048], or (n_real + 2) / 2 * n[0] > TWA_STATIC_SCRATCH_ELEMS (message via
-   twa_last_error(NULL)); TWA_ECUDA on a CUDA failure. */
+   and race.  Errors: TWA_EINVAL when psi is not 16-byte aligned, grid->dim != 1, precision !=
+   TWA_F32, n[0] is not a power of two in [8, 2048], (n_real + 2) / 2 * n[0] >
+   TWA_STATIC_SCRATCH_ELEMS, or (n_real + 2) / 2 > 65535 (message via twa_last_error(NULL)); all
+   of these are found before anything is launched.  TWA_ECUDA on a CUDA failure (a failed launch
+   of the Poisson passes returns before psi is touched). */
 #define TWA_STATIC_SCRATCH_ELEMS (1 << 19)
 int twa_step_batch_1d_static(const twa_grid* grid, const twa_params* p, int n_real, void* psi,
                              int n_steps, void* stream);

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -110,15 +111,21 @@ int pass(int N, int op, int lines, dim3 grid, const PassArgs& a, cudaStream_t st
 extern "C" int twa_step_batch_1d_static(const twa_grid* grid, const twa_params* p, int n_real, void* psi,
                                         int n_steps, void* stream) {
     if (!grid || !p || !psi || n_real < 1 || n_steps < 0) return fail(TWA_EINVAL, "null pointer or bad count");
+    // the line passes read and write the batch with 16-byte accesses, as the handle calls do
+    if (reinterpret_cast<uintptr_t>(psi) & 15u) return fail(TWA_EINVAL, "psi must be 16-byte aligned");
     if (grid->dim != 1 || p->precision != TWA_F32) return fail(TWA_EINVAL, "only 1D grids on the FP32 path");
     const int N = grid->n[0];
     if (N < 8 || N > kMaxN || (N & (N - 1))) return fail(TWA_EINVAL, "n[0] must be a power of two in [8, 2048]");
     if (!(p->hbar_m > 0) || !(p->dt > 0) || !(grid->L > 0)) return fail(TWA_EINVAL, "hbar_m, dt and L must be positive");
-    const int n_slots = n_real + 1, n_pairs = (n_slots + 1) / 2;
-    if ((long long)n_pairs * N > kScratchElems)
-        return fail(TWA_EINVAL, "pairs x n = " + std::to_string((long long)n_pairs * N) +
+    // counts in 64 bits: n_real near INT_MAX must not wrap before the size check
+    const long long n_slots_ll = (long long)n_real + 1, n_pairs_ll = (n_slots_ll + 1) / 2;
+    if (n_pairs_ll * N > kScratchElems)
+        return fail(TWA_EINVAL, "pairs x n = " + std::to_string(n_pairs_ll * N) +
                                     " exceeds the static scratch of " + std::to_string(kScratchElems) +
                                     " complex values (TWA_STATIC_SCRATCH_ELEMS)");
+    // the Poisson passes put one pair per grid row (grid.y <= 65535)
+    if (n_pairs_ll > 65535) return fail(TWA_EINVAL, "more than 65535 stream pairs");
+    const int n_slots = (int)n_slots_ll, n_pairs = (int)n_pairs_ll;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -175,6 +182,8 @@ extern "C" int twa_step_batch_1d_static(const twa_grid* grid, const twa_params* 
     // Poisson field of the synchronized batch (overwrites whatever the last call left)
     if (int rc = pass(N, OP_RHO_FWD, 1, dim3(1, n_pairs, 1), a, st)) return rc;
     if (int rc = pass(N, OP_MUL_INV, 1, dim3(1, n_pairs, 1), a, st)) return rc;
+    // a failed launch of the Poisson passes must not let the steps below touch psi
+    if (const cudaError_t e0 = cudaGetLastError(); e0 != cudaSuccess) return fail(TWA_ECUDA, cudaGetErrorString(e0));
     // n_steps on chip with the opening half kick, then the closing half kick
     const int T = plan_threads_per_line(N);
     const int lines = (128 / T) > 1 ? 128 / T : 1;

@@ -61,13 +61,66 @@ def test_moments_of_the_initial_coherent_state():
 
 
 def test_free_field_twa_is_exact():
-    # quadratic H: every |a_k|^2 is conserved stream by stream, and so is Q
+    # quadratic H: every |a_k|^2 is conserved stream by stream, and so are Q and Var n_k
     g, psi = _bump(64)
     n = 1e3
     t, series, _ = twa.run(psi, 0.05, 0.0, 0.01, 1.0, 1, n, 16, 9, 30, 10)
     for s in series[1:]:
         assert np.max(np.abs(s["nk_mean"] - series[0]["nk_mean"])) < 1e-9
+        assert np.max(np.abs(s["nk_var"] - series[0]["nk_var"])) < 1e-9 * (1 + np.max(series[0]["nk_var"]))
         assert abs(s["Q"] - series[0]["Q"]) < 1e-12
+
+
+def test_free_field_keeps_the_coherent_state_moments_at_late_times():
+    # the TWA is exact for the free field: <n_k> = Var n_k = |z_k|^2 at every t (here after 200
+    # steps, long after every mode has rotated many times), within the sampling error
+    g, psi = _bump(32)
+    n, Ns = 50.0, 20000
+    t, series, _ = twa.run(psi, 0.2, 0.0, 0.01, 1.0, 1, n, Ns, 5, 200, 200)
+    m = series[-1]
+    z2 = np.abs(np.fft.fft(psi) * math.sqrt(n * g.dV / g.cells)) ** 2
+    assert np.all(np.abs(m["nk_mean"] - z2) < 5 * np.sqrt((z2 + 0.25) / Ns))
+    assert np.all(np.abs(m["nk_var"] - z2) < 6 * (np.sqrt((2 * z2 ** 2 + 4 * z2 + 1) / Ns) + 1e-3))
+
+
+def test_correction_norm_of_constructed_batches():
+    # streams psi0 e^{i theta_s}: every |psi_s|^2 = rho_cl, so <rho> - rho_cl = -1/(2 n dV) in every
+    # cell and corr = sqrt(M) / (2 n dV ||rho_cl||); streams c_s psi0 (real c_s) give
+    # <rho> - rho_cl = (mean c^2 - 1) rho_cl - 1/(2 n dV)
+    M, n_tot, L = 32, 1e3, 2.0
+    dV = L / M
+    rng = np.random.default_rng(9)
+    psi0 = (1.0 + rng.random(M)) * np.exp(1j * rng.uniform(0, 2 * np.pi, M))
+    w = 1.0 / (2.0 * n_tot * dV)
+    rho = np.abs(psi0) ** 2
+    theta = np.array([0.3, -1.2, 2.0])
+    rot = np.concatenate([psi0[None], psi0[None] * np.exp(1j * theta)[:, None]])
+    m = twa.moments(rot, n_tot, L, 1, with_modes=False)
+    assert m["corr"] == pytest.approx(math.sqrt(M) * w / np.linalg.norm(rho), rel=1e-12)
+    c = np.array([0.9, 1.05, 1.2, 0.7])
+    sc = np.concatenate([psi0[None], c[:, None] * psi0[None]])
+    m = twa.moments(sc, n_tot, L, 1, with_modes=False)
+    expect = np.linalg.norm((np.mean(c ** 2) - 1.0) * rho - w) / np.linalg.norm(rho)
+    assert m["corr"] == pytest.approx(expect, rel=1e-12)
+
+
+def test_correction_norm_of_the_initial_coherent_state():
+    # At t = 0, psi_s = psi_cl + d_s with complex Gaussian d_s of variance 2 sigma^2 = 1/(2 n dV):
+    # X_s = |psi_cl + d_s|^2 - rho_cl - 1/(2 n dV) has mean 0 and variance 4 sigma^2 rho_cl + 4 sigma^4
+    # per cell, so E ||<rho> - rho_cl||^2 = sum_g (4 sigma^2 rho_g + 4 sigma^4) / N_s.  A missing Weyl
+    # offset adds M / (2 n dV)^2 (five times the expectation here); a wrong noise variance doubles it.
+    g, psi = _bump(64)
+    n, Ns, R = 50.0, 16, 400
+    sig2 = 1.0 / (4.0 * n * g.dV)
+    rho = np.abs(psi) ** 2
+    expect = np.sum(4 * sig2 * rho + 4 * sig2 ** 2) / Ns
+    vals = []
+    for r in range(R):
+        m = twa.moments(twa.sample(psi, 1000 + r, Ns, n, g.dV), n, 1.0, 1, with_modes=False)
+        vals.append((m["corr"] * np.linalg.norm(rho)) ** 2)
+    vals = np.array(vals)
+    assert abs(vals.mean() - expect) < 5 * vals.std() / math.sqrt(R)
+    assert abs(vals.mean() - expect) < 0.05 * expect
 
 
 def test_nsQs_is_independent_of_the_sampling_n():
@@ -91,6 +144,10 @@ def _fock_case(M, C=200.0, amp=0.9, n=10.0, times=(0.0, 0.02, 0.05)):
 
 
 def _twa_nk(psi, C, n, times, Ns, noise_conv=0, dt=1e-3):
+    """<n_k> and Var n_k of the TWA ensemble from oracle.twa.moments, with standard errors.
+
+    The standard errors are the test's own: the spread of |a_k|^2 over the streams for <n_k>, and
+    the delta-method influence function of the Var n_k estimator for Var n_k."""
     M = psi.size
     cur = twa.sample(psi, 7, Ns, n, 1.0 / M, noise_conv)
     res = []
@@ -99,17 +156,17 @@ def _twa_nk(psi, C, n, times, Ns, noise_conv=0, dt=1e-3):
         while s < int(round(t / dt)):
             cur = sp.step(cur, 1.0, C, dt, 1.0, 1)
             s += 1
+        mo = twa.moments(cur, n, 1.0, 1)
         a = np.fft.fft(cur, axis=-1) * math.sqrt(n * (1.0 / M) / M)
         a2 = np.abs(a[1:]) ** 2
         m2 = a2.mean(0)
-        var = (a2 ** 2).mean(0) - m2 - (m2 - 0.5) ** 2
         infl = a2 ** 2 - a2 - 2 * (m2 - 0.5) * a2            # delta-method influence function
-        res.append((m2 - 0.5, a2.std(0) / math.sqrt(Ns), var, infl.std(0) / math.sqrt(Ns),
+        res.append((mo["nk_mean"], a2.std(0) / math.sqrt(Ns), mo["nk_var"], infl.std(0) / math.sqrt(Ns),
                     np.abs(a[0]) ** 2))
     return res
 
 
-@pytest.mark.parametrize("M", [2, 3])
+@pytest.mark.parametrize("M", [2, 3, 4])
 def test_twa_matches_brute_force_fock_evolution(M):
     psi, C, n, times = _fock_case(M)
     nk, var, prob = fock.mode_occupations(psi, 1.0, 1.0, C, n, times, n_max=40)
