@@ -347,29 +347,49 @@ def _one_d_rate():
 
 def _uneven_rate(steps=3):
     """Uneven multi-instance batch in one handle (2D two-soliton merger: 512^2 x 128, 1024^2 x 64 and
-    2048^2 x 16 streams), moments every 10 steps, the instances on parallel graph branches."""
-    import tempfile
+    2048^2 x 16 streams), moments every 10 steps: the tuned batch mode, then each mode (one instance
+    after another, parallel graph branches, one persistent launch per interval) and each instance in
+    a handle of its own (the sum of the parts)."""
     import torch
     import twa_inputs as ti
-    from paper_2310_07119_gb300 import Ensemble, twa_advance
+    from paper_2310_07119_gb300 import (BATCH_FORK, BATCH_PERSISTENT, BATCH_SERIAL, Ensemble, twa_advance,
+                                        twa_get_batch_mode, twa_set_batch_mode)
     ws = [ti.workload_2d_merger(m, nr, 1000) for m, nr in ((512, 128), (1024, 64), (2048, 16))]
     p = ws[0].phys
+
+    def timed(ens):
+        ens.sample([w.psi_cl() for w in ws] if len(ens.grids) == len(ws) else [ens._w.psi_cl()], SEED)
+        twa_advance(ens.h, ens.psi, 2 * OUT_EVERY, OUT_EVERY, ens.new_series(2 * OUT_EVERY, OUT_EVERY))
+        series = ens.new_series(steps * OUT_EVERY, OUT_EVERY)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        twa_advance(ens.h, ens.psi, steps * OUT_EVERY, OUT_EVERY, series)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
     ens = Ensemble([w.grid for w in ws], p.hbar_m, p.C, p.dt, p.n_tot, [w.n_real for w in ws], want_modes=True)
     ens.autotune(_tune_cache_path(torch.cuda.current_device()))
-    ens.sample([w.psi_cl() for w in ws], SEED)
-    warm = ens.new_series(2 * OUT_EVERY, OUT_EVERY)
-    twa_advance(ens.h, ens.psi, 2 * OUT_EVERY, OUT_EVERY, warm)
-    series = ens.new_series(steps * OUT_EVERY, OUT_EVERY)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    twa_advance(ens.h, ens.psi, steps * OUT_EVERY, OUT_EVERY, series)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    tuned = twa_get_batch_mode(ens.h)
+    ms = timed(ens)
+    modes = {}
+    for name, m in (("serial", BATCH_SERIAL), ("fork", BATCH_FORK), ("persistent", BATCH_PERSISTENT)):
+        twa_set_batch_mode(ens.h, m)
+        modes[name] = timed(ens)
     ens.close()
-    cu = sum(w.n_real * w.grid.cells for w in ws) * OUT_EVERY * steps
-    return {"value": cu / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+    alone = []
+    for w in ws:
+        e = Ensemble([w.grid], p.hbar_m, p.C, p.dt, p.n_tot, [w.n_real], want_modes=True)
+        e._w = w
+        e.autotune(_tune_cache_path(torch.cuda.current_device()))
+        alone.append(timed(e))
+        e.close()
+    cu = sum(w.n_real * w.grid.cells for w in ws) * OUT_EVERY
+    return {"value": cu * steps / (ms * steps * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "tuned_mode": ["serial", "fork", "persistent"][tuned],
+            "ms_per_step_by_mode": modes, "ms_per_step_instances_alone": alone,
+            "ms_per_step_sum_of_parts": sum(alone),
             "workload": "2D two-soliton merger 512^2 x 128 + 1024^2 x 64 + 2048^2 x 16 streams in one handle, "
                         f"{OUT_EVERY} KDK steps + moments per step, batch {sum((w.n_real + 1) * w.grid.cells for w in ws) * 8 / 1e9:.2f} GB"}
 

@@ -270,9 +270,39 @@ const char* twa_fno_last_error(const twa_fno* f);
 int twa_fno_features(const double* nk_cl, const double* nk_est, const double* nk_ref, double n_tot, int grid,
                      float* x, float* t, void* stream);
 
-/* Block on `stream` and report device-side failures recorded since the last call
-   (TWA_ENONFINITE) or TWA_OK.  Clears the device error word. */
+/* Block on `stream` and report device-side failures recorded since the last call (TWA_ETIMEOUT: a
+   bounded wait of the persistent launch gave up; TWA_ENONFINITE) or TWA_OK.  Clears the device
+   error word. */
 int twa_sync_status(twa_handle* h, void* stream);
+
+/* How the instances of a batch run their steps (chosen by twa_autotune, or set here):
+     TWA_BATCH_SERIAL     : one instance after another, one launch per pass;
+     TWA_BATCH_FORK       : instances on parallel streams (parallel graph branches);
+     TWA_BATCH_PERSISTENT : every step of every instance in one persistent launch per call (per output
+                            interval of twa_advance) that walks a work list of (step, pass, instance,
+                            pair of streams, tile of lines) items, Sec. III.A's independent streams
+                            scheduled as data flow: an item starts once its pair's earlier passes are
+                            done, so passes of different pairs and instances overlap.  Available for FP32
+                            handles whose instances are all 2D with axes of 256 to 2048 cells and carry
+                            no test particles (TWA_EINVAL otherwise).  Its device-side waits are bounded
+                            (twa_set_wait_limit); a wait that runs out stops the launch and
+                            twa_sync_status reports TWA_ETIMEOUT (the batch's fields are then undefined).
+   The pass profiler runs the passes one by one whatever the mode.  twa_get_batch_mode returns the mode. */
+#define TWA_BATCH_SERIAL      0
+#define TWA_BATCH_FORK        1
+#define TWA_BATCH_PERSISTENT  2
+int twa_set_batch_mode(twa_handle* h, int mode);
+int twa_get_batch_mode(const twa_handle* h);
+
+/* Longest time a CTA of the persistent launch waits for a dependency before it gives up (default 2 s,
+   0 < seconds <= 60; counted in SM clock cycles at the device's peak clock). */
+int twa_set_wait_limit(twa_handle* h, double seconds);
+
+/* Fault injection for tests of the failure path: the next persistent launch of this handle waits for
+   one tile that no work item produces, so its waits run out after the wait limit, the launch stops and
+   twa_sync_status reports TWA_ETIMEOUT.  Nothing faults: the GPU stays usable and later calls run
+   normally.  TWA_EINVAL if the handle has no persistent launch. */
+int twa_debug_stall_next_batch(twa_handle* h);
 
 /* Message of the last failure on this handle (or of the last twa_create failure if h is NULL). */
 const char* twa_last_error(const twa_handle* h);

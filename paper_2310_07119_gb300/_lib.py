@@ -16,6 +16,7 @@ TWA_OK, TWA_EINVAL, TWA_ENOMEM, TWA_ECUDA, TWA_ETIMEOUT, TWA_ENONFINITE = 0, -1,
 TWA_F32, TWA_F64_PLAIN = 0, 1
 TWA_NSCALARS = 8
 TWA_OBS_OF_MEAN, TWA_OBS_MODES, TWA_OBS_FP32 = 1, 2, 4
+TWA_BATCH_SERIAL, TWA_BATCH_FORK, TWA_BATCH_PERSISTENT = 0, 1, 2
 SCALAR_NAMES = ("Q", "corr", "mass", "mass_cl", "nonfinite", "nk_sum", "drho_l2", "rhocl_l2")
 # Pass kinds of the FP32 pipelines, in the library's numbering (profiler ops).
 PASS_NAMES = ("drift", "kick_drift", "kick_drift_vinv", "drift_rho", "rho_fwd", "fwd", "fwd_mul_inv", "inv",
@@ -63,6 +64,10 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "twa_sync_status": (ctypes.c_int, [_P, _P]),
+    "twa_set_batch_mode": (ctypes.c_int, [_P, ctypes.c_int]),
+    "twa_get_batch_mode": (ctypes.c_int, [_P]),
+    "twa_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
+    "twa_debug_stall_next_batch": (ctypes.c_int, [_P]),
     "twa_last_error": (ctypes.c_char_p, [_P]),
     "twa_autotune": (ctypes.c_int, [_P, _P, ctypes.c_char_p, _P]),
     "twa_last_launch_count": (ctypes.c_longlong, [_P]),

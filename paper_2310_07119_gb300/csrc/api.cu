@@ -31,7 +31,9 @@
 #include "kernels.h"
 #include "observable.h"
 #include "passes.cuh"
+#include "batch.h"
 #include "pipe.cuh"
+#include "run1d.cuh"
 #include "twa.h"
 
 using namespace twa;
@@ -61,6 +63,8 @@ struct Inst {
     float* k2[3] = {nullptr, nullptr, nullptr};
     double* part_r = nullptr;
     double* part_m = nullptr;
+    double* run_part = nullptr;  // partial sums of whole 1D runs (k_run1d)
+    size_t run_part_n = 0;
     std::map<int, int> lines;  // (axis * 64 + op) -> lines per CTA
     // test particles (FP32 path): state [n_slots][r 3, p 3] and the spectral derivative kernels
     double* prt = nullptr;
@@ -105,6 +109,20 @@ struct twa_handle {
     int g_out_every = -1;
     // run the instances of a multi-instance batch on parallel streams (see Fork)
     bool fork = false;
+    // run the steps of all instances as one persistent launch over a work list (2D batches)
+    bool persist = false;
+    double wait_limit_s = 2.0;     // longest device-side wait of the persistent launch
+    bool stall_next = false;       // fault injection: the next persistent launch waits forever
+    unsigned* d_ctr = nullptr;     // per-pair tile counters of the persistent launch
+    unsigned long long* d_tick = nullptr;  // [0] ticket, [1] abort flag (low word)
+    struct BatchTable {
+        twa::BatchPass* passes;
+        twa::PassArgs* args;
+        int n_passes;
+        long long n_items;
+        std::vector<int> kinds;
+    };
+    std::vector<std::pair<std::vector<double>, BatchTable>> btab;
     // pass profiler
     bool prof_on = false;
     struct ProfRec {
@@ -281,21 +299,10 @@ int prof_events(twa_handle* h, cudaEvent_t* a, cudaEvent_t* b) {
     return 0;
 }
 
-// One line pass over `fields` fields (pairs or slots) of instance I.
-int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_frac, float2* buf, float2* out, int fields,
-             cudaStream_t st, int nsteps = 0, int force_lines = 0, float post = 1.0f) {
+// Arguments of a line pass along `axis` of instance I.
+PassArgs make_args(twa_handle* h, Inst& I, float2* psi, int axis, double kick_frac, float2* buf, float2* out,
+                   int nsteps = 0, float post = 1.0f) {
     const int N = I.n[axis];
-    const bool strided = axis > 0;
-    int lines = force_lines;
-    if (!lines) {
-        auto it = I.lines.find(key_of(axis, op));
-        lines = (it != I.lines.end()) ? it->second : default_lines(N, strided, op);
-    }
-    const bool pipe = (lines & PIPE_FLAG) != 0;
-    if (!variant_ok(N, op, strided, lines))
-        return fail(h, TWA_EINVAL, "no pass variant for N=" + std::to_string(N) + " op=" + std::to_string(op) +
-                                       " lines=" + std::to_string(lines));
-    lines &= ~PIPE_FLAG;
     PassArgs a{};
     a.psi = psi;
     a.buf = buf;
@@ -320,6 +327,26 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
     a.S = (int)stride;
     a.Qn = (int)stride;
     a.OS = stride * N;
+    return a;
+}
+
+// One line pass over `fields` fields (pairs or slots) of instance I.
+int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_frac, float2* buf, float2* out, int fields,
+             cudaStream_t st, int nsteps = 0, int force_lines = 0, float post = 1.0f) {
+    const int N = I.n[axis];
+    const bool strided = axis > 0;
+    int lines = force_lines;
+    if (!lines) {
+        auto it = I.lines.find(key_of(axis, op));
+        lines = (it != I.lines.end()) ? it->second : default_lines(N, strided, op);
+    }
+    const bool pipe = (lines & PIPE_FLAG) != 0;
+    if (!variant_ok(N, op, strided, lines))
+        return fail(h, TWA_EINVAL, "no pass variant for N=" + std::to_string(N) + " op=" + std::to_string(op) +
+                                       " lines=" + std::to_string(lines));
+    lines &= ~PIPE_FLAG;
+    const PassArgs a = make_args(h, I, psi, axis, kick_frac, buf, out, nsteps, post);
+    const long long stride = a.S;
     LaunchCfg c{};
     c.op = op;
     c.strided = strided;
@@ -566,6 +593,116 @@ struct Fork {
         return 0;
     }
 };
+
+// ---------------------------------------------------------------------------------------------
+// Persistent batch launch (batch.cu): the steps of every instance of a 2D FP32 batch as one launch
+// over a work list of (step, pass, instance, pair, tile) items.
+
+// Every instance is 2D with both axis lengths in [256, 2048] and has no test particles.
+bool batch_eligible(const twa_handle* h) {
+    if (h->p.precision != TWA_F32 || h->in.empty()) return false;
+    for (const auto& I : h->in)
+        if (I.mode != MODE_2D || I.prt || batch_kind(I.n[0], 0) < 0 || batch_kind(I.n[1], 1) < 0) return false;
+    return true;
+}
+bool use_batch(const twa_handle* h) { return h->persist && !h->prof_on && batch_eligible(h); }
+
+// The work list of n steps (first kick a_first) of the batch psi, built once per (psi, n, a_first,
+// dt) and kept: the list lives in device memory the launches read, so it is created before any
+// stream capture and never rewritten while a launch may read it.
+int batch_table(twa_handle* h, void* psi, int n, double a_first, cudaStream_t st, twa_handle::BatchTable** out) {
+    const bool stall = h->stall_next;
+    const std::vector<double> key = {(double)reinterpret_cast<uintptr_t>(psi), (double)n, a_first, h->p.dt};
+    if (!stall)
+        for (auto& e : h->btab)
+            if (e.first == key) {
+                *out = &e.second;
+                return 0;
+            }
+    std::vector<BatchPass> P;
+    std::vector<PassArgs> A;
+    std::vector<int> kinds;
+    std::vector<int> ctr_base, argi, tiles(h->in.size() * 4), tsum(h->in.size());
+    int nctr = 0;
+    for (size_t i = 0; i < h->in.size(); ++i) {
+        Inst& I = h->in[i];
+        float2* f = inst_psi(I, psi);
+        ctr_base.push_back(nctr);
+        nctr += I.n_pairs;
+        argi.push_back((int)A.size());
+        // pass arguments: x rows (first step's kick, later kicks), y columns, x rows, y columns
+        A.push_back(make_args(h, I, f, 0, a_first, I.vc, nullptr));
+        A.push_back(make_args(h, I, f, 0, 1.0, I.vc, nullptr));
+        A.push_back(make_args(h, I, f, 1, 0.0, I.vc, nullptr));
+        A.push_back(make_args(h, I, f, 0, 0.0, I.vc, nullptr));
+        A.push_back(make_args(h, I, f, 1, 0.0, I.vc, nullptr));
+        for (int q = 0; q < 4; ++q) {
+            const int ax = q & 1, N = I.n[ax], L = batch_lines(N);
+            const long long lines = I.cells / N;  // rows (x) or columns (y) of the field
+            tiles[4 * i + q] = (int)((lines + L - 1) / L);
+            tsum[i] += tiles[4 * i + q];
+            const int k = batch_kind(N, q);
+            if (std::find(kinds.begin(), kinds.end(), k) == kinds.end()) kinds.push_back(k);
+        }
+    }
+    long long tick = 0;
+    for (int st_ = 0; st_ < n; ++st_)
+        for (int q = 0; q < 4; ++q)
+            for (size_t i = 0; i < h->in.size(); ++i) {
+                const Inst& I = h->in[i];
+                int pre = st_ * tsum[i];
+                for (int r = 0; r < q; ++r) pre += tiles[4 * i + r];
+                BatchPass b{};
+                b.first = tick;
+                b.kind = batch_kind(I.n[q & 1], q);
+                b.tiles = tiles[4 * i + q];
+                // one tile per ticket: several tiles per ticket (up to 16) measured slower on the
+                // uneven 2D mix (70.6 against 56.3 ms per 10 steps), longer items leaving CTAs idle
+                b.per_item = 1;
+                b.items = (b.tiles + b.per_item - 1) / b.per_item;
+                b.fields = I.n_pairs;
+                b.args = argi[i] + (q == 0 ? (st_ == 0 ? 0 : 1) : q + 1);
+                b.ctr = ctr_base[i];
+                b.target = pre;
+                P.push_back(b);
+                tick += (long long)b.items * b.fields;
+            }
+    if (stall && P.size() > h->in.size()) P[h->in.size()].target += 1;  // a tile that no item produces
+    if (!h->d_ctr) RC(dalloc(h, &h->d_ctr, (size_t)nctr));
+    if (!h->d_tick) RC(dalloc(h, &h->d_tick, 2));
+    twa_handle::BatchTable T{};
+    RC(dalloc(h, &T.passes, P.size()));
+    RC(dalloc(h, &T.args, A.size()));
+    CU(cudaMemcpyAsync(T.passes, P.data(), P.size() * sizeof(BatchPass), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(T.args, A.data(), A.size() * sizeof(PassArgs), cudaMemcpyHostToDevice, st));
+    T.n_passes = (int)P.size();
+    T.n_items = tick;
+    T.kinds = kinds;
+    h->btab.push_back({stall ? std::vector<double>{-1.0} : key, T});
+    *out = &h->btab.back().second;
+    return 0;
+}
+
+// n KDK steps (first kick a_first) of every instance in one persistent launch.
+int batch_steps(twa_handle* h, void* psi, int n, double a_first, cudaStream_t st) {
+    if (n <= 0) return 0;
+    twa_handle::BatchTable* T = nullptr;
+    RC(batch_table(h, psi, n, a_first, st, &T));
+    h->stall_next = false;
+    size_t nctr = 0;
+    for (const auto& I : h->in) nctr += (size_t)I.n_pairs;
+    CU(cudaMemsetAsync(h->d_ctr, 0, nctr * sizeof(unsigned), st));
+    CU(cudaMemsetAsync(h->d_tick, 0, 2 * sizeof(unsigned long long), st));
+    int dev = 0, khz = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const long long budget = (long long)(h->wait_limit_s * (double)khz * 1e3);
+    if (launch_batch(T->passes, T->n_passes, T->args, h->d_ctr, h->d_tick, T->n_items, h->d_err,
+                     reinterpret_cast<int*>(h->d_tick + 1), budget, T->kinds.data(), (int)T->kinds.size(), st) != 0)
+        return fail(h, TWA_ECUDA, "persistent batch launch: cudaFuncSetAttribute failed");
+    ++h->launches;
+    return 0;
+}
 
 // Moments with a pending kick (0 for a synchronized batch); scalars into `scalars` (device).
 int moments_f32(twa_handle* h, Inst& I, float2* psi, double pend, const twa_moments_out* o, double* scalars,
@@ -889,6 +1026,13 @@ int twa_step_batch(twa_handle* h, void* psi, int n_steps, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     h->launches = 0;
     if (n_steps == 0) return TWA_OK;
+    if (use_batch(h)) {
+        for (auto& I : h->in) RC(poisson_init(h, I, inst_psi(I, psi), st));
+        RC(batch_steps(h, psi, n_steps, 0.5, st));
+        for (auto& I : h->in) RC(closing_kick(h, I, inst_psi(I, psi), 0.5, st));
+        CU(cudaGetLastError());
+        return TWA_OK;
+    }
     Fork fk{h, st, false};
     RC(fk.open(h->in.size()));
     for (size_t i = 0; i < h->in.size(); ++i) {
@@ -931,6 +1075,16 @@ namespace {
 
 // One output interval of the FP32 run for all instances: steps, moments (pending half kick), store.
 int run_interval_f32(twa_handle* h, void* psi, int out_every, double a_first, double* series, cudaStream_t st) {
+    if (use_batch(h)) {
+        RC(batch_steps(h, psi, out_every, a_first, st));
+        for (size_t i = 0; i < h->in.size(); ++i) {
+            Inst& I = h->in[i];
+            RC(moments_f32(h, I, inst_psi(I, psi), 0.5, nullptr, h->d_cur + i * TWA_NSCALARS, st));
+        }
+        launch_store_series(h->d_cur, series, h->d_counter, (int)h->in.size() * TWA_NSCALARS, st);
+        ++h->launches;
+        return 0;
+    }
     Fork fk{h, st, false};
     RC(fk.open(h->in.size()));
     for (size_t i = 0; i < h->in.size(); ++i) {
@@ -1014,6 +1168,73 @@ int adaptive_dt(twa_handle* h, void* psi, double c_f, cudaStream_t st, double* d
     return 0;
 }
 
+// Whole 1D runs (run1d.cuh): every instance 1D, no test particles, the pass profiler off.
+bool run1d_eligible(const twa_handle* h) {
+    if (h->p.precision != TWA_F32 || h->prof_on) return false;
+    for (const auto& I : h->in)
+        if (I.mode != MODE_1D || I.prt) return false;
+    return true;
+}
+
+int dispatch_run1d(int N, const Run1DArgs& r, cudaStream_t st) {
+    switch (N) {
+        case 8: return launch_run1d<8>(r, st);
+        case 16: return launch_run1d<16>(r, st);
+        case 32: return launch_run1d<32>(r, st);
+        case 64: return launch_run1d<64>(r, st);
+        case 128: return launch_run1d<128>(r, st);
+        case 256: return launch_run1d<256>(r, st);
+        case 512: return launch_run1d<512>(r, st);
+        case 1024: return launch_run1d<1024>(r, st);
+        case 2048: return launch_run1d<2048>(r, st);
+        default: return -1;
+    }
+}
+
+// n_out output intervals of out_every steps of every (1D) instance of a synchronized batch, with
+// the scalars of outputs 0..n_out written to series: one on-chip launch per instance and chunk of
+// outputs (the partial sums are kept under 256 MB per instance) plus one finishing launch.
+int run1d_all(twa_handle* h, void* psi, int n_out, int out_every, double* series, cudaStream_t st) {
+    const int ni = (int)h->in.size();
+    for (int i = 0; i < ni; ++i) {
+        Inst& I = h->in[i];
+        const long long N = I.cells, P = I.n_pairs;
+        const long long per_out = P * 3 * N + N + P;
+        const long long cap = std::max(1LL, (256LL << 20) / (8 * per_out) - 1);
+        const int chunk = (int)std::min<long long>(std::max(n_out, 1), cap);
+        const size_t need = (size_t)(chunk + 1) * per_out;
+        if (I.run_part_n < need) {
+            RC(dalloc(h, &I.run_part, need));
+            I.run_part_n = need;
+        }
+        double* part = I.run_part;
+        double* part_cl = part + (size_t)(chunk + 1) * P * 3 * N;
+        double* part_bad = part_cl + (size_t)(chunk + 1) * N;
+        const double inv_ns = 1.0 / (double)I.n_real, weyl = 1.0 / (2.0 * h->p.n_tot * I.dV);
+        const double q_off = (double)I.cells / (2.0 * h->p.n_tot), nm = h->p.want_modes ? h->p.n_tot : 0.0;
+        int done = 0;
+        do {
+            const int k = std::min(chunk, n_out - done);
+            Run1DArgs r{};
+            r.a = make_args(h, I, inst_psi(I, psi), 0, 0.5, I.vc, nullptr);
+            r.n_out = k;
+            r.out_every = out_every;
+            r.part = part;
+            r.part_cl = part_cl;
+            r.part_bad = part_bad;
+            if (dispatch_run1d((int)N, r, st) != 0) return fail(h, TWA_ECUDA, "1D run: kernel attribute setup failed");
+            ++h->launches;
+            // the first chunk reports its initial output; later chunks start where the last one ended
+            const int skip = done == 0 ? 0 : 1;
+            launch_finish_run1d(part + skip * P * 3 * N, part_cl + skip * N, part_bad + skip * P, (int)P, (int)N,
+                                k + 1 - skip, inv_ns, weyl, I.dV, q_off, nm, series, done + skip, i, ni, h->d_err, st);
+            ++h->launches;
+            done += k;
+        } while (done < n_out);
+    }
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1046,6 +1267,11 @@ int twa_advance(twa_handle* h, void* psi_work, int n_steps, int out_every, doubl
         CU(cudaGetLastError());
         return TWA_OK;
     }
+    if (run1d_eligible(h)) {
+        RC(run1d_all(h, psi_work, n_out, out_every, series, user));
+        CU(cudaGetLastError());
+        return TWA_OK;
+    }
     // FP32: eager prologue and first interval, then one captured graph per later interval.
     const double kh = 0.5, kf = 1.0;
     for (size_t i = 0; i < h->in.size(); ++i) {
@@ -1067,6 +1293,11 @@ int twa_advance(twa_handle* h, void* psi_work, int n_steps, int out_every, doubl
             if (h->gexec) {
                 cudaGraphExecDestroy(h->gexec);
                 h->gexec = nullptr;
+            }
+            if (use_batch(h)) {
+                // the persistent launch's work list is uploaded outside the capture
+                twa_handle::BatchTable* T = nullptr;
+                RC(batch_table(h, psi_work, out_every, kf, user, &T));
             }
             CU(cudaEventRecord(h->ev_a, user));
             CU(cudaStreamWaitEvent(h->cap, h->ev_a, 0));
@@ -1257,11 +1488,49 @@ int twa_sync_status(twa_handle* h, void* stream) {
     int w = 0;
     CU(cudaMemcpy(&w, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     CU(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (w & TWA_ERR_TIMEOUT_BIT)
+        return fail(h, TWA_ETIMEOUT, "a device-side wait of the persistent batch launch gave up (wait limit " +
+                                         std::to_string(h->wait_limit_s) + " s); the batch's fields are undefined");
     if (w & 1) return fail(h, TWA_ENONFINITE, "a moments pass met a non-finite field value");
     return TWA_OK;
 }
 
 const char* twa_last_error(const twa_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int twa_set_batch_mode(twa_handle* h, int mode) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (mode < TWA_BATCH_SERIAL || mode > TWA_BATCH_PERSISTENT) return fail(h, TWA_EINVAL, "twa_set_batch_mode: bad mode");
+    if (mode == TWA_BATCH_PERSISTENT && !batch_eligible(h))
+        return fail(h, TWA_EINVAL,
+                    "twa_set_batch_mode: the persistent launch needs FP32 2D instances with axes of 256 to 2048 cells "
+                    "and no test particles");
+    h->fork = mode == TWA_BATCH_FORK;
+    h->persist = mode == TWA_BATCH_PERSISTENT;
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return TWA_OK;
+}
+
+int twa_get_batch_mode(const twa_handle* h) {
+    if (!h) return TWA_EINVAL;
+    return h->persist ? TWA_BATCH_PERSISTENT : (h->fork ? TWA_BATCH_FORK : TWA_BATCH_SERIAL);
+}
+
+int twa_set_wait_limit(twa_handle* h, double seconds) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!(seconds > 0.0) || seconds > 60.0) return fail(h, TWA_EINVAL, "twa_set_wait_limit: need 0 < seconds <= 60");
+    h->wait_limit_s = seconds;
+    return TWA_OK;
+}
+
+int twa_debug_stall_next_batch(twa_handle* h) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (!batch_eligible(h)) return fail(h, TWA_EINVAL, "twa_debug_stall_next_batch: the handle has no persistent launch");
+    h->stall_next = true;
+    return TWA_OK;
+}
 
 }  // extern "C"
 
@@ -1594,18 +1863,22 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
         }
         CU(cudaMemsetAsync(I.vc, 0, (size_t)I.n_pairs * I.cells * sizeof(float2), st));
     }
-    if (h->in.size() > 1) {
-        // multi-instance batch: time two steps of all instances forked and one after another
+    const bool can_persist = batch_eligible(h);
+    if (h->in.size() > 1 || can_persist) {
+        // how the instances run: one after another (0), on parallel streams (1, several instances),
+        // or as one persistent launch over a work list (2, 2D batches); two steps of each are timed
         std::string key = "batch";
         for (const auto& I : h->in)
             key += ":" + std::to_string(I.n[0]) + "x" + std::to_string(I.n[1]) + "x" + std::to_string(I.n[2]) +
                    "s" + std::to_string(I.n_slots);
         auto hit = cache.find(key);
-        if (hit != cache.end()) {
-            h->fork = hit->second != 0;
+        if (hit != cache.end() && (hit->second != 2 || can_persist) && (hit->second != 1 || h->in.size() > 1)) {
+            h->fork = hit->second == 1;
+            h->persist = hit->second == 2;
         } else {
-            float t[2] = {0.f, 0.f};
+            float t[3] = {0.f, 1e30f, 1e30f};
             auto steps_all = [&](int n) -> int {
+                if (h->persist) return batch_steps(h, psi, n, 1.0, st);
                 Fork fk{h, st, false};
                 RC(fk.open(h->in.size()));
                 for (size_t i = 0; i < h->in.size(); ++i) {
@@ -1616,8 +1889,10 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
                 }
                 return 0;
             };
-            for (int m = 0; m < 2; ++m) {
+            for (int m = 0; m < 3; ++m) {
+                if ((m == 1 && h->in.size() < 2) || (m == 2 && !can_persist)) continue;
                 h->fork = (m == 1);
+                h->persist = (m == 2);
                 RC(steps_all(1));
                 CU(cudaEventRecord(e0, st));
                 RC(steps_all(2));
@@ -1625,8 +1900,13 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
                 CU(cudaEventSynchronize(e1));
                 CU(cudaEventElapsedTime(&t[m], e0, e1));
             }
-            h->fork = t[1] < 0.97f * t[0];
-            cache[key] = h->fork ? 1 : 0;
+            // a mode other than one-after-another is kept only when it is clearly faster (3 %)
+            int best = 0;
+            for (int m = 1; m < 3; ++m)
+                if (t[m] < 0.97f * t[best]) best = m;
+            h->fork = best == 1;
+            h->persist = best == 2;
+            cache[key] = best;
         }
         for (auto& I : h->in) CU(cudaMemsetAsync(I.vc, 0, (size_t)I.n_pairs * I.cells * sizeof(float2), st));
     }

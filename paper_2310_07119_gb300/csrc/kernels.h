@@ -23,6 +23,10 @@ int launch_moments_modes(const float2* spec, long long cells, int n_slots, doubl
 int launch_finish_scalars(const double* part_r, int nb_r, const double* part_m, int nb_m, double dV,
                           double q_offset, double* scalars, int* err_word, cudaStream_t st);
 int launch_store_series(const double* cur, double* series, int* counter, int n, cudaStream_t st);
+// scalars of outputs row0 .. row0 + n_outputs - 1 of one instance of a whole 1D run (k_run1d partials)
+int launch_finish_run1d(const double* part, const double* part_cl, const double* part_bad, int n_pairs, int N,
+                        int n_outputs, double inv_ns, double weyl, double dV, double q_offset, double n_tot_modes,
+                        double* series, int row0, int inst, int n_inst, int* err_word, cudaStream_t st);
 // max over the batch of |re| and |im| of n complex values, folded into *vmax (float bits; *vmax must
 // start at 0 or at an earlier maximum)
 int launch_max_abs(const float2* buf, long long n, unsigned* vmax, cudaStream_t st);

@@ -407,6 +407,58 @@ __global__ void k_finish_scalars(const double* __restrict__ part_r, int nb_r, co
     }
 }
 
+// Scalars of every output of a whole 1D run (block o = output o): per cell the pair partials of
+// the run kernel added in pair order, then the cell sums of k_finish_scalars in a fixed tree order.
+// Sum_k <n_k> follows from the streams' mass by Parseval's identity for the unitary DFT:
+// sum_k mean|a_k|^2 = n_tot sum_g dV mean|psi_g|^2 (only written when modes are on, as elsewhere).
+__global__ void k_finish_run1d(const double* __restrict__ part, const double* __restrict__ part_cl,
+                               const double* __restrict__ part_bad, int n_pairs, int N, double inv_ns, double weyl,
+                               double dV, double q_offset, double n_tot_modes, double* series, int row0, int inst,
+                               int n_inst, int* err_word) {
+    const int o = blockIdx.x;
+    double v[NP_REAL] = {0, 0, 0, 0, 0, 0};
+    for (int g = threadIdx.x; g < N; g += blockDim.x) {
+        double m2 = 0.0, pr = 0.0, pi = 0.0;
+        for (int p = 0; p < n_pairs; ++p) {
+            const double* pp = part + ((long long)o * n_pairs + p) * 3 * N;
+            m2 += pp[g];
+            pr += pp[N + g];
+            pi += pp[2 * N + g];
+        }
+        m2 *= inv_ns;
+        pr *= inv_ns;
+        pi *= inv_ns;
+        const double cl = part_cl[(long long)o * N + g], rm = m2 - weyl;
+        v[0] += m2 - (pr * pr + pi * pi);
+        v[1] += (rm - cl) * (rm - cl);
+        v[2] += cl * cl;
+        v[3] += m2;
+        v[4] += cl;
+    }
+    for (int p = threadIdx.x; p < n_pairs; p += blockDim.x) v[5] += part_bad[(long long)o * n_pairs + p];
+    __shared__ double red[NP_REAL][256];
+    for (int j = 0; j < NP_REAL; ++j) red[j][threadIdx.x] = v[j];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int j = 0; j < NP_REAL; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double* sc = series + ((long long)(row0 + o) * n_inst + inst) * 8;
+        const double d2 = sqrt(red[1][0]), c2 = sqrt(red[2][0]);
+        sc[0] = red[0][0] * dV - q_offset;
+        sc[1] = d2 / c2;
+        sc[2] = red[3][0] * dV;
+        sc[3] = red[4][0] * dV;
+        sc[4] = red[5][0];
+        sc[5] = n_tot_modes > 0.0 ? n_tot_modes * sc[2] - 0.5 * N : 0.0;
+        sc[6] = d2;
+        sc[7] = c2;
+        if (red[5][0] > 0.0 && err_word) atomicOr(err_word, 1);
+    }
+}
+
 // Copy the current output's scalars into series[counter] and advance the device counter (keeps a
 // captured graph identical across replays).
 __global__ void k_store_series(const double* __restrict__ cur, double* series, int* counter, int n) {
@@ -495,6 +547,13 @@ int launch_particles(const float2* W, long long cells, const int* n, int dim, do
                      double fscale, double kick_dt, double drift_dt, int n_slots, double* prt, cudaStream_t st) {
     k_particles<<<n_slots, 128, 0, st>>>(W, cells, n[0], n[1], n[2], dim, L, ker[0], ker[1], ker[2], fscale, kick_dt,
                                          drift_dt, prt);
+    return 0;
+}
+int launch_finish_run1d(const double* part, const double* part_cl, const double* part_bad, int n_pairs, int N,
+                        int n_outputs, double inv_ns, double weyl, double dV, double q_offset, double n_tot_modes,
+                        double* series, int row0, int inst, int n_inst, int* err_word, cudaStream_t st) {
+    k_finish_run1d<<<n_outputs, 256, 0, st>>>(part, part_cl, part_bad, n_pairs, N, inv_ns, weyl, dV, q_offset,
+                                              n_tot_modes, series, row0, inst, n_inst, err_word);
     return 0;
 }
 int launch_store_series(const double* cur, double* series, int* counter, int n, cudaStream_t st) {

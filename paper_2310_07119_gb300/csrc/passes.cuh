@@ -153,14 +153,15 @@ __host__ __device__ constexpr bool op_stash(int op) {
            op == OP_KICK_DRIFT || op == OP_KICK_FWD_OUT;
 }
 
+// One tile of a line pass: LINES lines of field f (tile index bx along the field), run by the
+// LINES * T threads of the CTA with dynamic shared memory smem.  Kernel body of k_line, and the
+// work item of the persistent batch kernel.
 template <int N, int LINES, bool STRIDED, int OP>
-__global__ void __launch_bounds__(LINES * Plan<N>::T, (OP == OP_STEPS_1D) ? 1 : min_ctas(LINES * Plan<N>::T))
-k_line(const PassArgs a) {
+__device__ __forceinline__ void line_tile(const PassArgs& a, int bx, int f, float2* smem) {
     using P = Plan<N>;
     constexpr int T = P::T, RMAX = P::RMAX, LS = STRIDED ? line_stride(N, LINES) : line_stride_rows(N, T);
     constexpr bool WARP = !STRIDED && (T <= 32);
     constexpr unsigned MASK = (LINES * T >= 32) ? 0xffffffffu : ((1u << (LINES * T)) - 1u);
-    extern __shared__ float2 smem[];
     const int tid = threadIdx.x;
     const int l = STRIDED ? (tid % LINES) : (tid / T);
     const int t = STRIDED ? (tid / LINES) : (tid % T);
@@ -186,17 +187,16 @@ k_line(const PassArgs a) {
     bool act;
     if constexpr (STRIDED) {
         const int tq = (a.Qn + LINES - 1) / LINES;
-        const int q = (int)(blockIdx.x % tq) * LINES + l;
+        const int q = (int)(bx % tq) * LINES + l;
         act = q < a.Qn;
-        base = (act ? q : a.Qn - 1) + (int)(blockIdx.x / tq) * (int)a.OS;
+        base = (act ? q : a.Qn - 1) + (int)(bx / tq) * (int)a.OS;
     } else {
         const int rows = (int)(a.cells / N);
-        const int row = (int)blockIdx.x * LINES + l;
+        const int row = (int)bx * LINES + l;
         act = row < rows;
         base = (act ? row : rows - 1) * N;
     }
     const int S = STRIDED ? a.S : 1;
-    const int f = blockIdx.y;
     float2 v[RMAX];
 
     // The pair passes ask L2 for the stream lines they read after another field (the potential, or
@@ -205,16 +205,16 @@ k_line(const PassArgs a) {
     auto prefetch_lines = [&](const float2* F) {
         if constexpr (STRIDED) {
             const int tq = (a.Qn + LINES - 1) / LINES;
-            const int q0 = (int)(blockIdx.x % tq) * LINES;
+            const int q0 = (int)(bx % tq) * LINES;
             const unsigned bytes = (unsigned)min(LINES, a.Qn - q0) * 8u;
-            const float2* b0 = F + q0 + (long long)(blockIdx.x / tq) * a.OS;
+            const float2* b0 = F + q0 + (long long)(bx / tq) * a.OS;
             // one short segment per position: plain per-thread prefetches, one per 32-byte sector
             for (int j = tid; j < N; j += NTH) {
                 const char* p = reinterpret_cast<const char*>(b0 + (long long)j * S);
                 for (unsigned o = 0; o < bytes; o += 32u) prefetch_l2_sector(p + o);
             }
         } else {
-            const int r0 = (int)blockIdx.x * LINES;
+            const int r0 = (int)bx * LINES;
             const unsigned bytes = (unsigned)min(LINES, (int)(a.cells / N) - r0) * N * 8u;
             const char* b0 = reinterpret_cast<const char*>(F + (long long)r0 * N);
             if (((reinterpret_cast<uintptr_t>(b0) | bytes) & 15u) == 0)
@@ -391,7 +391,7 @@ k_line(const PassArgs a) {
         store_nat(v, F);
     } else if constexpr (OP == OP_STEPS_1D) {
         // base is the line offset inside the field; here each line slot of the CTA is one pair.
-        const int p = (int)blockIdx.x * LINES + l;
+        const int p = (int)bx * LINES + l;
         const bool active = p < a.n_pairs;
         const int pe = active ? p : a.n_pairs - 1;
         const bool has1 = 2 * pe + 1 < a.n_slots;
@@ -436,6 +436,13 @@ k_line(const PassArgs a) {
             }
         }
     }
+}
+
+template <int N, int LINES, bool STRIDED, int OP>
+__global__ void __launch_bounds__(LINES * Plan<N>::T, (OP == OP_STEPS_1D) ? 1 : min_ctas(LINES * Plan<N>::T))
+k_line(const PassArgs a) {
+    extern __shared__ float2 smem[];
+    line_tile<N, LINES, STRIDED, OP>(a, (int)blockIdx.x, (int)blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -19,11 +19,13 @@ __all__ = [
     "twa_moments", "twa_run", "twa_sync_status", "twa_last_error", "twa_autotune",
     "twa_last_launch_count", "twa_poisson_multiplier", "twa_observable_create", "twa_observable_eval",
     "twa_observable_destroy", "Observable", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_particles_set", "twa_particles_get", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
-    "F64_PLAIN", "SCALAR_NAMES", "PASS_NAMES",
+    "F64_PLAIN", "SCALAR_NAMES", "PASS_NAMES", "twa_set_batch_mode", "twa_get_batch_mode", "twa_set_wait_limit",
+    "twa_debug_stall_next_batch", "BATCH_SERIAL", "BATCH_FORK", "BATCH_PERSISTENT",
 ]
 
 F32, F64_PLAIN = L.TWA_F32, L.TWA_F64_PLAIN
 SCALAR_NAMES = L.SCALAR_NAMES
+BATCH_SERIAL, BATCH_FORK, BATCH_PERSISTENT = L.TWA_BATCH_SERIAL, L.TWA_BATCH_FORK, L.TWA_BATCH_PERSISTENT
 PASS_NAMES = L.PASS_NAMES
 
 
@@ -174,9 +176,26 @@ def twa_profile_read(h) -> dict:
 
 def twa_sync_status(h, stream=None) -> int:
     rc = _lib().twa_sync_status(h, _stream(stream))
-    if rc not in (0, L.TWA_ENONFINITE):
+    if rc not in (0, L.TWA_ENONFINITE, L.TWA_ETIMEOUT):
         _check(rc, h)
     return rc
+
+
+def twa_set_batch_mode(h, mode: int) -> None:
+    """Run the instances' steps one after another, forked, or as one persistent launch (include/twa.h)."""
+    _check(_lib().twa_set_batch_mode(h, int(mode)), h)
+
+
+def twa_get_batch_mode(h) -> int:
+    return int(_lib().twa_get_batch_mode(h))
+
+
+def twa_set_wait_limit(h, seconds: float) -> None:
+    _check(_lib().twa_set_wait_limit(h, float(seconds)), h)
+
+
+def twa_debug_stall_next_batch(h) -> None:
+    _check(_lib().twa_debug_stall_next_batch(h), h)
 
 
 def twa_last_error(h) -> str:
