@@ -465,8 +465,14 @@ def run_twa(args):
     ens = Ensemble([w.grid], w.phys.hbar_m, w.phys.C, w.phys.dt, w.phys.n_tot, [ns], want_modes=True,
                    device=f"cuda:{local}")
     cl = w.psi_cl()
+    tuned = {}
     if not args.no_tune:
         ens.autotune(_tune_cache_path(local))
+        try:
+            key = f"{GRID_M}x{GRID_M}x{GRID_M}:slots{ns + 1}:"
+            tuned = {k[len(key):]: v for k, v in json.load(open(_tune_cache_path(local))).items() if k.startswith(key)}
+        except (OSError, ValueError):
+            tuned = {}
     ens.sample([cl], w.noise_seed)
     series_w = ens.new_series(max(1, args.warmup) * OUT_EVERY, OUT_EVERY)
     twa_advance(ens.h, ens.psi, max(1, args.warmup) * OUT_EVERY, OUT_EVERY, series_w)
@@ -537,6 +543,9 @@ def run_twa(args):
                                    "replay); the roofline and per-pass figures come from this run",
                            "clocks": clocks_prof},
         "passes": passes,
+        "tuned_passes": {"lines_per_cta_by_axis_op": tuned,
+                         "flags": "65536: cp.async-pipelined variant; 131072: two-field variant; axis9 op0: 3D "
+                                  "pipeline (0 axis passes, 1 xy-plane passes)"},
         "gpu_launches": int(launches),
         "moments_last": {"Q": float(sc[-1, 0, 0]), "corr": float(sc[-1, 0, 1]), "mass": float(sc[-1, 0, 2])},
         "clocks": clocks,
@@ -558,6 +567,8 @@ def run_twa(args):
         torch.cuda.empty_cache()
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                                 "sample": f"2 streams of the 128^3 workload, {n} KDK steps in {el:.1f} s (FP64 scipy.fft)"}
+        torch.cuda.empty_cache()
+        line["paper_scale_512"] = _paper_scale()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

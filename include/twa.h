@@ -263,12 +263,34 @@ int twa_fno_adamw(twa_fno* f, float lr, float beta1, float beta2, float eps, flo
 /* mean squared error of y against t (n floats) into *loss (device float); dy (optional) = dL/dy */
 int twa_fno_mse(twa_fno* f, const float* y, const float* t, long long n, float* loss, float* dy, void* stream);
 const char* twa_fno_last_error(const twa_fno* f);
+/* The contractions along the contiguous axis of the truncated DFT (the forward transform of the
+   real input rows and the real part of the adjoint's last axis) run as GEMMs on the tensor cores
+   (TF32 operands, FP32 accumulation; see twa_tc_gemm) when their shapes allow: the forward when grid
+   is a multiple of 32 (up to 128), the adjoint when 4 modes is.  twa_fno_tensor_core_shapes returns
+   which (bit 0 forward, bit 1 adjoint); twa_fno_set_tensor_cores(f, 0) routes both back to the
+   CUDA-core kernels (for comparisons).  twa_fno_sync_status blocks on `stream` and reports
+   TWA_ETIMEOUT if a bounded wait of those GEMMs gave up since the last call, else TWA_OK. */
+int twa_fno_set_tensor_cores(twa_fno* f, int on);
+int twa_fno_tensor_core_shapes(const twa_fno* f);
+int twa_fno_sync_status(twa_fno* f, void* stream);
+
 /* Input features x[4][grid^3] of one snapshot from device FP64 per-mode occupations (FFT order),
    with nu = n_tot / grid^3: x0 = log10(1 + n_cl) / 8, x1 = (n_est - n_cl) / (n_cl + nu) (the
    few-stream correction estimate, relative), x2 = log10(n_tot) - 9, x3 = |m| / (grid/2); and, if t is
    not NULL, the target t[grid^3] = (n_ref - n_cl) / (n_cl + nu) from a reference ensemble. */
 int twa_fno_features(const double* nk_cl, const double* nk_est, const double* nk_ref, double n_tot, int grid,
                      float* x, float* t, void* stream);
+
+/* Tensor-core GEMM of tall-skinny FP32 matrices (no counterpart in the paper; the surrogate's DFT
+   contractions use it, and tests call it directly): C[p][j] (+ C[p][j] if accumulate) =
+   sum_k A[p][k] Bt[j][k] for p < P, j < N.  A: device, row stride lda floats; Bt: device [Np][K],
+   rows N..Np-1 ignored (zero them); C: device, row stride ldc floats.  Operands are rounded to TF32
+   (10-bit mantissa) by the tensor cores, products summed in FP32 in tensor memory (tcgen05); A and Bt
+   tiles are moved by TMA.  Shapes: K a multiple of 32 up to 128, Np a multiple of 16 in [16, 256]
+   with 128 K (256 + Np) + 1024 <= 232448 bytes of tiles (Np <= 192 at K = 128); A and Bt 16-byte aligned, lda * 4 a multiple of 16 (TWA_EINVAL otherwise).  Asynchronous on stream;
+   a device-side wait that runs out (2 s) sets bit 4 of *err (device int). */
+int twa_tc_gemm(const float* A, long long P, long long K, long long lda, const float* Bt, int N, int Np, float* C,
+                long long ldc, int accumulate, int* err, void* stream);
 
 /* Block on `stream` and report device-side failures recorded since the last call (TWA_ETIMEOUT: a
    bounded wait of the persistent launch gave up; TWA_ENONFINITE) or TWA_OK.  Clears the device

@@ -88,6 +88,11 @@ _SIGS = {
     "twa_fno_mse": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P, _P, _P]),
     "twa_fno_last_error": (ctypes.c_char_p, [_P]),
     "twa_fno_features": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P, _P, _P]),
+    "twa_fno_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int]),
+    "twa_fno_tensor_core_shapes": (ctypes.c_int, [_P]),
+    "twa_fno_sync_status": (ctypes.c_int, [_P, _P]),
+    "twa_tc_gemm": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, _P, ctypes.c_int,
+                                   ctypes.c_int, _P, ctypes.c_longlong, ctypes.c_int, _P, _P]),
 }
 
 _lib = None

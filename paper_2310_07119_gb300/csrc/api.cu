@@ -237,6 +237,7 @@ int dispatch(int N, const LaunchCfg& c, const PassArgs& a, cudaStream_t st, bool
 }
 
 constexpr int PIPE_FLAG = 1 << 16;  // "lines" values with this bit select the pipelined pass
+constexpr int DUAL_FLAG = 1 << 17;  // ... and with this bit the two-field variant (both slots of a pair)
 
 int dispatch_pipe(int N, const LaunchCfg& c, const PassArgs& a, int tiles, int n_items, cudaStream_t st, bool prep) {
     switch (N) {
@@ -264,8 +265,25 @@ bool pipe_variant_ok(int N, int op, bool strided, int lines) {
     }
 }
 
+bool dual_variant_ok(int N, int op, bool strided, int lines) {
+    switch (N) {
+        case 8: return has_dual_variant<8>(op, strided, lines);
+        case 16: return has_dual_variant<16>(op, strided, lines);
+        case 32: return has_dual_variant<32>(op, strided, lines);
+        case 64: return has_dual_variant<64>(op, strided, lines);
+        case 128: return has_dual_variant<128>(op, strided, lines);
+        case 256: return has_dual_variant<256>(op, strided, lines);
+        case 512: return has_dual_variant<512>(op, strided, lines);
+        case 1024: return has_dual_variant<1024>(op, strided, lines);
+        case 2048: return has_dual_variant<2048>(op, strided, lines);
+        default: return false;
+    }
+}
+
 bool variant_ok(int N, int op, bool strided, int lines) {
+    if ((lines & PIPE_FLAG) && (lines & DUAL_FLAG)) return false;
     if (lines & PIPE_FLAG) return pipe_variant_ok(N, op, strided, lines & ~PIPE_FLAG);
+    if (lines & DUAL_FLAG) return dual_variant_ok(N, op, strided, lines & ~DUAL_FLAG);
     switch (N) {
         case 8: return has_variant<8>(op, strided, lines);
         case 16: return has_variant<16>(op, strided, lines);
@@ -341,16 +359,21 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
         lines = (it != I.lines.end()) ? it->second : default_lines(N, strided, op);
     }
     const bool pipe = (lines & PIPE_FLAG) != 0;
+    const bool dual = (lines & DUAL_FLAG) != 0;
     if (!variant_ok(N, op, strided, lines))
         return fail(h, TWA_EINVAL, "no pass variant for N=" + std::to_string(N) + " op=" + std::to_string(op) +
                                        " lines=" + std::to_string(lines));
-    lines &= ~PIPE_FLAG;
+    lines &= ~(PIPE_FLAG | DUAL_FLAG);
+    // the two-field drift runs over pairs of slots
+    const int slot_fields = fields;
+    if (dual && op == OP_DRIFT) fields = (fields + 1) / 2;
     const PassArgs a = make_args(h, I, psi, axis, kick_frac, buf, out, nsteps, post);
     const long long stride = a.S;
     LaunchCfg c{};
     c.op = op;
     c.strided = strided;
     c.lines = lines;
+    c.dual = dual;
     if (op == OP_STEPS_1D) {
         c.grid = dim3((unsigned)((I.n_pairs + lines - 1) / lines), 1, 1);
     } else if (strided) {
@@ -369,8 +392,8 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
         if (lines_per_field % lines != 0 || (strided && stride % lines != 0))
             return fail(h, TWA_EINVAL, "pipelined pass needs full tiles");
     }
-    const long long pk = ((long long)pipe << 41) | ((long long)N << 24) | ((long long)op << 16) |
-                         ((long long)strided << 12) | lines;
+    const long long pk = ((long long)dual << 42) | ((long long)pipe << 41) | ((long long)N << 24) |
+                         ((long long)op << 16) | ((long long)strided << 12) | lines;
     if (!h->prepared.count(pk)) {
         const int rc = pipe ? dispatch_pipe(N, c, a, tiles, n_items, st, true) : dispatch(N, c, a, st, true);
         if (rc != 0) return fail(h, TWA_ECUDA, "cudaFuncSetAttribute failed");
@@ -385,7 +408,7 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
         return fail(h, TWA_EINVAL, "pass dispatch failed");
     if (h->prof_on) {
         CU(cudaEventRecord(e1, st));
-        const long long nf = (op == OP_STEPS_1D) ? (long long)I.n_pairs * nsteps : (long long)fields;
+        const long long nf = (op == OP_STEPS_1D) ? (long long)I.n_pairs * nsteps : (long long)slot_fields;
         h->prof_pending.push_back({op, e0, e1, nf, I.cells});
     }
     ++h->launches;
@@ -1756,13 +1779,14 @@ int time_variant(twa_handle* h, Inst& I, float2* f, const TunePass& ps, int l, c
 int tune_passes(twa_handle* h, Inst& I, float2* f, const std::vector<TunePass>& passes, std::map<std::string, int>& cache,
                 cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
     const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512, PIPE_FLAG | 1, PIPE_FLAG | 2, PIPE_FLAG | 4,
-                        PIPE_FLAG | 8, PIPE_FLAG | 16, PIPE_FLAG | 32, PIPE_FLAG | 64};
+                        PIPE_FLAG | 8, PIPE_FLAG | 16, PIPE_FLAG | 32, PIPE_FLAG | 64, DUAL_FLAG | 4, DUAL_FLAG | 8,
+                        DUAL_FLAG | 16, DUAL_FLAG | 32, DUAL_FLAG | 64, DUAL_FLAG | 128, DUAL_FLAG | 256};
     for (const auto& ps : passes) {
         const int N = I.n[ps.axis == 3 ? 0 : ps.axis];
         auto ok = [&](int l) {
             if (ps.axis == 3) return (l & PIPE_FLAG) == 0 && plane_variant_ok(N, ps.op, l);
             if (!variant_ok(N, ps.op, ps.axis > 0, l)) return false;
-            const int ll = l & ~PIPE_FLAG;
+            const int ll = l & ~(PIPE_FLAG | DUAL_FLAG);
             if (l & PIPE_FLAG) {
                 long long stride = 1;
                 for (int b = 0; b < ps.axis; ++b) stride *= I.n[b];

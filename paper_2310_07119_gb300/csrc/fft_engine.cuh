@@ -366,6 +366,73 @@ struct FftStage {
     }
 };
 
+// The same stage on two lines held by the same threads (the two fields of a pair), interleaved: each
+// twiddle is read once for both.  The table reads are the largest share of the shared-memory
+// wavefronts of the heavy passes (a 128-bit read costs four per warp, whatever its broadcast), so
+// serving two fields per read relieves the L1 data pipe those passes are bound by.
+template <int N, bool INV, int s, bool WARP, unsigned MASK, bool TS = false>
+struct FftStage2 {
+    using P = Plan<N>;
+    static constexpr int RMAX = P::RMAX, T = P::T, S = P::S;
+    using SI = StageInfo<N, INV, s>;
+    static constexpr int R = SI::R, NS = SI::NS;
+    static constexpr int TWO = tw_offset<N, INV, s>();
+
+    __device__ __forceinline__ static void run(float2 (&v)[RMAX], float2 (&u)[RMAX], int t, float2* smv, float2* smu,
+                                               const float4* __restrict__ tw) {
+        constexpr int B = RMAX / R;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int j = t + T * b;
+            if constexpr (NS > 1) {
+                const int k = j & (NS - 1);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float4 w = TS ? tw[TWO + (r - 1) * NS + k] : __ldg(&tw[TWO + (r - 1) * NS + k]);
+                    const float2 hi = INV ? make_float2(w.x, -w.y) : make_float2(w.x, w.y);
+                    const float2 lo = INV ? make_float2(w.z, -w.w) : make_float2(w.z, w.w);
+                    v[b * R + r] = cmul_c(v[b * R + r], hi, lo);
+                    u[b * R + r] = cmul_c(u[b * R + r], hi, lo);
+                }
+            }
+            dft<R, INV>(&v[b * R]);
+            dft<R, INV>(&u[b * R]);
+        }
+        if constexpr (s + 1 < S) {
+            constexpr int R2 = StageInfo<N, INV, s + 1>::R;
+            constexpr int B2 = RMAX / R2;
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int j = t + T * b;
+                const int base = (j / NS) * NS * R + (j & (NS - 1));
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    smv[pad_n(N, base + r * NS)] = v[b * R + r];
+                    smu[pad_n(N, base + r * NS)] = u[b * R + r];
+                }
+            }
+            line_sync<WARP, MASK>();
+#pragma unroll
+            for (int b = 0; b < B2; ++b) {
+                const int j = t + T * b;
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    v[b * R2 + r] = smv[pad_n(N, j + r * (N / R2))];
+                    u[b * R2 + r] = smu[pad_n(N, j + r * (N / R2))];
+                }
+            }
+            line_sync<WARP, MASK>();
+            FftStage2<N, INV, s + 1, WARP, MASK, TS>::run(v, u, t, smv, smu, tw);
+        }
+    }
+};
+
+template <int N, bool INV, bool WARP, unsigned MASK = 0xffffffffu, bool TS = false>
+__device__ __forceinline__ void fft_line2(float2 (&v)[Plan<N>::RMAX], float2 (&u)[Plan<N>::RMAX], int t, float2* smv,
+                                          float2* smu, const float4* __restrict__ tw) {
+    FftStage2<N, INV, 0, WARP, MASK, TS>::run(v, u, t, smv, smu, tw);
+}
+
 // Forward (INV = false) or inverse transform of one line held as in pos_nat / pos_spec.
 template <int N, bool INV, bool WARP, unsigned MASK = 0xffffffffu, bool TS = false>
 __device__ __forceinline__ void fft_line(float2 (&v)[Plan<N>::RMAX], int t, float2* sm, const float4* __restrict__ tw) {

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "reduce.cuh"
+#include "tc_gemm.h"
 #include "twa.h"
 
 void twa_set_global_error(const std::string& msg);
@@ -242,6 +243,13 @@ struct twa_fno {
     long long step = 0;
     float2* Mf[3] = {nullptr, nullptr, nullptr};  // forward truncated DFT per axis (2m x n)
     float2* Mi[3] = {nullptr, nullptr, nullptr};  // adjoint (n x 2m)
+    // the x-axis (contiguous) contractions as real GEMMs on the tensor cores (tc_gemm.cu):
+    // Bf [npf][n]: rows (Re, Im) of the 2m DFT rows; Ba [npa][4m]: per cell the (Re, -Im) of its adjoint row
+    float* Bf = nullptr;
+    float* Ba = nullptr;
+    int npf = 0, npa = 0;
+    bool tc_fwd = false, tc_adj = false, tc_on = true;
+    int* d_err = nullptr;
     // activations for the largest batch seen
     int cap_b = 0;
     std::vector<float*> h, z;
@@ -333,8 +341,12 @@ int ensure_batch(twa_fno* f, int B) {
 // A (truncated forward DFT) of a real [B*W][n][n][n] field into complex [B*W][2m][2m][2m].
 void dft_fwd(twa_fno* f, const float* in, float2* out, long long BW, cudaStream_t st) {
     const int n = f->cfg.grid, m2 = 2 * f->cfg.modes;
-    // x axis (last): (BW*n*n, n, 1) -> (BW*n*n, 2m, 1)
-    k_axis<<<blocks_for(BW * n * n * m2), kThreads, 0, st>>>(nullptr, in, f->Mf[2], f->t1, nullptr, BW * n * n, n, m2, 1, 0);
+    // x axis (last): (BW*n*n, n, 1) -> (BW*n*n, 2m, 1); on the tensor cores when the shape allows
+    if (!(f->tc_on && f->tc_fwd &&
+          twa::tc_gemm(in, BW * n * n, n, n, f->Bf, 2 * m2, f->npf, reinterpret_cast<float*>(f->t1), 2 * m2, 0, f->d_err,
+                  2.0, st) == 0))
+        k_axis<<<blocks_for(BW * n * n * m2), kThreads, 0, st>>>(nullptr, in, f->Mf[2], f->t1, nullptr, BW * n * n, n, m2, 1,
+                                                                  0);
     // y axis: (BW*n, n, 2m) -> (BW*n, 2m, 2m)
     k_axis<<<blocks_for(BW * n * m2 * m2), kThreads, 0, st>>>(f->t1, nullptr, f->Mf[1], f->t2, nullptr, BW * n, n, m2, m2, 0);
     // z axis: (BW, n, 4m^2) -> (BW, 2m, 4m^2)
@@ -348,8 +360,11 @@ void dft_adj(twa_fno* f, const float2* in, float* out, long long BW, int accumul
     k_axis<<<blocks_for(BW * n * m2 * m2), kThreads, 0, st>>>(in, nullptr, f->Mi[0], f->t1, nullptr, BW, m2, n,
                                                               (long long)m2 * m2, 0);
     k_axis<<<blocks_for(BW * n * n * m2), kThreads, 0, st>>>(f->t1, nullptr, f->Mi[1], f->t2, nullptr, BW * n, m2, n, m2, 0);
-    k_axis<<<blocks_for(BW * n * n * n), kThreads, 0, st>>>(f->t2, nullptr, f->Mi[2], nullptr, out, BW * n * n, m2, n, 1,
-                                                            accumulate);
+    if (!(f->tc_on && f->tc_adj &&
+          twa::tc_gemm(reinterpret_cast<const float*>(f->t2), BW * n * n, 2 * m2, 2 * m2, f->Ba, n, f->npa, out, n, accumulate,
+                  f->d_err, 2.0, st) == 0))
+        k_axis<<<blocks_for(BW * n * n * n), kThreads, 0, st>>>(f->t2, nullptr, f->Mi[2], nullptr, out, BW * n * n, m2, n,
+                                                                1, accumulate);
 }
 
 void pointwise(const float* X, const __nv_bfloat16* W, const float* b, float* Y, int B, int cin, int cout, long long K,
@@ -423,6 +438,33 @@ int twa_fno_create(twa_fno** out, const twa_fno_config* cfg, uint64_t seed) {
         if ((rc = falloc(f, &f->Mf[a], mf.size())) || (rc = falloc(f, &f->Mi[a], mi.size()))) return bail(rc);
         cudaMemcpy(f->Mf[a], mf.data(), mf.size() * sizeof(float2), cudaMemcpyHostToDevice);
         cudaMemcpy(f->Mi[a], mi.data(), mi.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    }
+    // real forms of the x-axis matrices for the tensor-core GEMMs (rows past 2 m2 / n stay zero)
+    f->npf = (2 * m2 + 15) / 16 * 16;
+    f->npa = (n + 15) / 16 * 16;
+    f->tc_fwd = twa::tc_gemm_supported(n, f->npf);
+    f->tc_adj = twa::tc_gemm_supported(2 * m2, f->npa);
+    if ((rc = falloc(f, &f->d_err, 1))) return bail(rc);
+    cudaMemset(f->d_err, 0, sizeof(int));
+    if (f->tc_fwd) {
+        std::vector<float> bf((size_t)f->npf * n, 0.f);
+        for (int i = 0; i < m2; ++i)
+            for (int j = 0; j < n; ++j) {
+                bf[(size_t)(2 * i) * n + j] = mf[(size_t)i * n + j].x;
+                bf[(size_t)(2 * i + 1) * n + j] = mf[(size_t)i * n + j].y;
+            }
+        if ((rc = falloc(f, &f->Bf, bf.size()))) return bail(rc);
+        cudaMemcpy(f->Bf, bf.data(), bf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (f->tc_adj) {
+        std::vector<float> ba((size_t)f->npa * 2 * m2, 0.f);
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < m2; ++i) {
+                ba[(size_t)j * 2 * m2 + 2 * i] = mi[(size_t)j * m2 + i].x;
+                ba[(size_t)j * 2 * m2 + 2 * i + 1] = -mi[(size_t)j * m2 + i].y;
+            }
+        if ((rc = falloc(f, &f->Ba, ba.size()))) return bail(rc);
+        cudaMemcpy(f->Ba, ba.data(), ba.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     // initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for pointwise maps, scale 1/(W^2) for R,
     // zero biases, from a fixed linear-congruential stream of the seed (host side)
@@ -565,6 +607,40 @@ int twa_fno_mse(twa_fno* f, const float* y, const float* t, long long n, float* 
 }
 
 const char* twa_fno_last_error(const twa_fno* f) { return f ? f->err.c_str() : ""; }
+
+int twa_fno_set_tensor_cores(twa_fno* f, int on) {
+    if (!f) return ffail(nullptr, TWA_EINVAL, "twa_fno_set_tensor_cores: null handle");
+    f->tc_on = on != 0;
+    return TWA_OK;
+}
+
+int twa_fno_tensor_core_shapes(const twa_fno* f) {
+    if (!f) return 0;
+    return (f->tc_fwd ? 1 : 0) | (f->tc_adj ? 2 : 0);
+}
+
+int twa_fno_sync_status(twa_fno* f, void* stream) {
+    if (!f) return ffail(nullptr, TWA_EINVAL, "twa_fno_sync_status: null handle");
+    FC(cudaStreamSynchronize((cudaStream_t)stream));
+    int w = 0;
+    FC(cudaMemcpy(&w, f->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    FC(cudaMemset(f->d_err, 0, sizeof(int)));
+    if (w & twa::TC_ERR_TIMEOUT_BIT) return ffail(f, TWA_ETIMEOUT, "a tensor-core GEMM wait gave up");
+    return TWA_OK;
+}
+
+int twa_tc_gemm(const float* A, long long P, long long K, long long lda, const float* Bt, int N, int Np, float* C,
+                long long ldc, int accumulate, int* err, void* stream) {
+    if (!A || !Bt || !C || !err || P <= 0 || N <= 0 || N > Np || lda < K || ldc < N)
+        return ffail(nullptr, TWA_EINVAL, "twa_tc_gemm: bad argument");
+    const int rc = twa::tc_gemm(A, P, K, lda, Bt, N, Np, C, ldc, accumulate, err, 2.0, (cudaStream_t)stream);
+    if (rc == -1)
+        return ffail(nullptr, TWA_EINVAL,
+                     "twa_tc_gemm: unsupported shape or alignment (K a multiple of 32 up to 128, Np a multiple of 16 "
+                     "in [16, 256], 16-byte aligned A and Bt, lda * 4 a multiple of 16)");
+    if (rc) return ffail(nullptr, TWA_ECUDA, "twa_tc_gemm: tensor map or launch failed");
+    return TWA_OK;
+}
 
 }  // extern "C"
 

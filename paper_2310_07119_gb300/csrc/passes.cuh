@@ -153,26 +153,49 @@ __host__ __device__ constexpr bool op_stash(int op) {
            op == OP_KICK_DRIFT || op == OP_KICK_FWD_OUT;
 }
 
+// Ops with a two-field variant (DUAL): both fields of a pair (slots 2f, 2f+1) are transformed by the
+// same threads at once, so every twiddle and kinetic-phase table read serves two fields; the drift
+// then runs over pairs instead of slots.
+__host__ __device__ constexpr bool op_dual(int op) {
+    return op == OP_DRIFT || op == OP_KICK_DRIFT || op == OP_KICK_DRIFT_VINV || op == OP_DRIFT_RHO;
+}
+
+// Shared-memory layout of a tile (offsets in float2): the exchange lines, the per-thread stash, the
+// staged tables (16-byte aligned) and, for DUAL, a second set of exchange lines.
+template <int N, int LINES, bool STRIDED, int OP, bool DUAL>
+struct TileSmem {
+    static constexpr int T = Plan<N>::T, RMAX = Plan<N>::RMAX, NTH = LINES * T;
+    static constexpr int LS = STRIDED ? line_stride(N, LINES) : line_stride_rows(N, T);
+    static constexpr bool TS = tables_in_smem<N, OP>() || (DUAL && N >= 16 && N <= 256);
+    static constexpr int stash = LINES * LS;
+    static constexpr int tables = (stash + (op_stash(OP) ? RMAX * NTH : 0) + 1) / 2 * 2;
+    static constexpr int ex2 = tables + (TS ? 2 * (tw_entries<N>() + N) : 0);
+    static constexpr int total = ex2 + (DUAL ? LINES * LS : 0);
+};
+
 // One tile of a line pass: LINES lines of field f (tile index bx along the field), run by the
 // LINES * T threads of the CTA with dynamic shared memory smem.  Kernel body of k_line, and the
 // work item of the persistent batch kernel.
-template <int N, int LINES, bool STRIDED, int OP>
+template <int N, int LINES, bool STRIDED, int OP, bool DUAL = false>
 __device__ __forceinline__ void line_tile(const PassArgs& a, int bx, int f, float2* smem) {
     using P = Plan<N>;
-    constexpr int T = P::T, RMAX = P::RMAX, LS = STRIDED ? line_stride(N, LINES) : line_stride_rows(N, T);
+    using SM = TileSmem<N, LINES, STRIDED, OP, DUAL>;
+    static_assert(!DUAL || op_dual(OP), "no two-field variant of this op");
+    constexpr int T = P::T, RMAX = P::RMAX, LS = SM::LS;
     constexpr bool WARP = !STRIDED && (T <= 32);
     constexpr unsigned MASK = (LINES * T >= 32) ? 0xffffffffu : ((1u << (LINES * T)) - 1u);
     const int tid = threadIdx.x;
     const int l = STRIDED ? (tid % LINES) : (tid / T);
     const int t = STRIDED ? (tid / LINES) : (tid % T);
     float2* sm = smem + l * LS;
+    float2* sm2 = smem + SM::ex2 + l * LS;  // second exchange line (DUAL)
     constexpr int NTH = LINES * T;
     const float4* tw = a.tw;
     const float4* ph = a.ph;
-    constexpr bool TS = tables_in_smem<N, OP>();
+    constexpr bool TS = SM::TS;
     if constexpr (TS) {
         constexpr int E = tw_entries<N>();
-        float4* st = reinterpret_cast<float4*>(smem + LINES * LS + (op_stash(OP) ? RMAX * NTH : 0));
+        float4* st = reinterpret_cast<float4*>(smem + SM::tables);
         for (int i = tid; i < E; i += NTH) st[i] = __ldg(&a.tw[i]);
         for (int i = tid; i < N; i += NTH) st[E + i] = __ldg(&a.ph[i]);
         __syncthreads();
@@ -273,8 +296,78 @@ __device__ __forceinline__ void line_tile(const PassArgs& a, int bx, int f, floa
         phase(w);
         fft_line<N, true, WARP, MASK, TS>(w, t, sm, tw);
     };
+    // both fields of a pair at once: one table read per twiddle and phase for the two
+    auto drift2 = [&](float2 (&w)[RMAX], float2 (&x)[RMAX]) {
+        fft_line2<N, false, WARP, MASK, TS>(w, x, t, sm, sm2, tw);
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+            const int k = pos_spec<N>(t, i);
+            const float4 p = TS ? ph[k] : __ldg(&ph[k]);
+            w[i] = cmul_c(w[i], make_float2(p.x, p.y), make_float2(p.z, p.w));
+            x[i] = cmul_c(x[i], make_float2(p.x, p.y), make_float2(p.z, p.w));
+        }
+        fft_line2<N, true, WARP, MASK, TS>(w, x, t, sm, sm2, tw);
+    };
 
-    if constexpr (OP == OP_DRIFT) {
+    if constexpr (DUAL) {
+        // field f is the pair (2f, 2f+1); a missing second slot is transformed as zeros and not stored
+        float2* F0 = a.psi + (long long)(2 * f) * a.cells;
+        float2* F1 = F0 + a.cells;
+        const bool has1 = 2 * f + 1 < a.n_slots;
+        float2 u[RMAX];
+        float* stv = reinterpret_cast<float*>(smem + SM::stash) + tid;
+        if constexpr (OP == OP_KICK_DRIFT_VINV || OP == OP_KICK_DRIFT) {
+            // the pair's potentials (inverse-transformed from the spectral Poisson line, or read real)
+            // parked in the stash as two float planes
+            const bool kick = OP == OP_KICK_DRIFT_VINV || a.kick != 0.f;
+            if (kick) {
+                if constexpr (OP == OP_KICK_DRIFT_VINV) {
+                    load_spec(v, a.buf + (long long)f * a.cells);
+                } else {
+                    load_nat(v, a.buf + (long long)f * a.cells);
+                }
+            }
+            prefetch_pair(kick);
+            if (kick) {
+                if constexpr (OP == OP_KICK_DRIFT_VINV) fft_line<N, true, WARP, MASK, TS>(v, t, sm, tw);
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) {
+                    stv[i * NTH] = v[i].x;
+                    stv[(RMAX + i) * NTH] = v[i].y;
+                }
+            }
+            load_nat(v, F0);
+            if (has1) load_nat(u, F1);
+            else {
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) u[i] = make_float2(0.f, 0.f);
+            }
+            if (kick) {
+                kick_all(v, a.kick, a.kick_lo, [&](int i) { return stv[i * NTH]; });
+                kick_all(u, a.kick, a.kick_lo, [&](int i) { return stv[(RMAX + i) * NTH]; });
+            }
+            drift2(v, u);
+            store_nat(v, F0);
+            if (has1) store_nat(u, F1);
+        } else {  // OP_DRIFT (over pairs), OP_DRIFT_RHO
+            load_nat(v, F0);
+            if (has1) load_nat(u, F1);
+            else {
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i) u[i] = make_float2(0.f, 0.f);
+            }
+            drift2(v, u);
+            store_nat(v, F0);
+            if (has1) store_nat(u, F1);
+            if constexpr (OP == OP_DRIFT_RHO) {
+#pragma unroll
+                for (int i = 0; i < RMAX; ++i)
+                    v[i] = make_float2(fmaf(v[i].x, v[i].x, v[i].y * v[i].y), fmaf(u[i].x, u[i].x, u[i].y * u[i].y));
+                fft_line<N, false, WARP, MASK, TS>(v, t, sm, tw);
+                store_spec(v, a.buf + (long long)f * a.cells);
+            }
+        }
+    } else if constexpr (OP == OP_DRIFT) {
         float2* F = a.psi + (long long)f * a.cells;
         load_nat(v, F);
         drift(v);
@@ -438,11 +531,11 @@ __device__ __forceinline__ void line_tile(const PassArgs& a, int bx, int f, floa
     }
 }
 
-template <int N, int LINES, bool STRIDED, int OP>
+template <int N, int LINES, bool STRIDED, int OP, bool DUAL = false>
 __global__ void __launch_bounds__(LINES * Plan<N>::T, (OP == OP_STEPS_1D) ? 1 : min_ctas(LINES * Plan<N>::T))
 k_line(const PassArgs a) {
     extern __shared__ float2 smem[];
-    line_tile<N, LINES, STRIDED, OP>(a, (int)blockIdx.x, (int)blockIdx.y, smem);
+    line_tile<N, LINES, STRIDED, OP, DUAL>(a, (int)blockIdx.x, (int)blockIdx.y, smem);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -581,11 +674,14 @@ struct LaunchCfg {
     bool strided;
     int lines;
     dim3 grid;
+    bool dual = false;  // two-field variant (both slots of a pair per thread; drift over pairs)
 };
 template <int N>
 int launch_line(const LaunchCfg& c, const PassArgs& a, cudaStream_t st, bool prepare_only);
 template <int N>
 bool has_variant(int op, bool strided, int lines);
+template <int N>
+bool has_dual_variant(int op, bool strided, int lines);
 int plan_threads_per_line(int n);
 
 }  // namespace twa

@@ -79,3 +79,23 @@ def test_soliton_256_cubed_sampled_streams():
     for _ in range(w.n_steps):
         ref = sp.step(ref, w.phys.hbar_m, w.phys.C, w.phys.dt, w.grid.L, 3)
     assert np.all(field_rel_l2(sub, ref, 3) < 1e-4), field_rel_l2(sub, ref, 3)
+
+
+def test_512_cubed_soliton_sampled_streams():
+    """The paper's 3D resolution (512^3, Sec. V) on the stable-object workload: the classical field
+    and two sampled streams, 5 KDK steps at the pi/4 step of the 512^3 grid, against the oracle (field
+    and per-stream density tolerances of the parity tests)."""
+    w = ti.workload_3d_soliton(512, 2, 5)
+    cl = w.psi_cl()
+    ens = make_ensemble([w], 0, want_modes=False)
+    ens.sample([cl], w.noise_seed)
+    ens.step(w.n_steps)
+    got = ens.fields(0).cpu().numpy().astype(np.complex128)
+    ens.close()
+    del ens
+    torch.cuda.empty_cache()
+    ref = oracle_batch(w, cl, w.n_steps)
+    assert np.all(field_rel_l2(got, ref, 3) < 1e-4), field_rel_l2(got, ref, 3)
+    r_got, r_ref = np.abs(got) ** 2, np.abs(ref) ** 2
+    rho_err = np.sqrt(np.sum((r_got - r_ref) ** 2, axis=(1, 2, 3)) / np.sum(r_ref ** 2, axis=(1, 2, 3)))
+    assert np.all(rho_err < 1e-5), rho_err

@@ -383,3 +383,57 @@ def test_pipelined_passes_match_oracle(name, axis_pipeline, tmp_path):
     got = ens.fields(0).cpu().numpy().astype(np.complex128)
     ref = oracle_batch(w, cl, w.n_steps)
     assert np.all(field_rel_l2(got, ref, w.grid.dim) < F32_FIELD_TOL)
+
+
+DUAL = 1 << 17     # flag on a pass's "lines" value selecting its two-field variant (both slots of a pair per thread)
+DUAL_OPS = (0, 1, 2, 3)     # drift, kick_drift, kick_drift_vinv, drift_rho
+
+
+def _force_dual(w, path, axis_pipeline, dual=True):
+    """Autotune cache that selects the 3D pipeline and, for every pass that has one, the two-field
+    variant (dual) or the single-field variant with the same lines per CTA."""
+    import json
+    n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)
+    key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
+    cache = {f"{key}:axis9:op0": 0 if axis_pipeline else 1}
+    for ax in range(w.grid.dim):
+        T = THREADS_PER_LINE.get(n[ax], 1)
+        lines = max(4 if ax > 0 else 2, 128 // T)
+        for op in DUAL_OPS:
+            cache[f"{key}:axis{ax}:op{op}"] = (DUAL if dual else 0) | lines
+    json.dump(cache, open(path, "w"))
+
+
+@pytest.mark.parametrize("name,axis_pipeline", [("3d_kgauss64", True), ("3d_kgauss64_odd", True),
+                                                ("3d_kgauss64", False), ("2d_merger64", True), ("2d_merger2048", True)])
+def test_dual_passes_match_oracle_and_the_single_field_passes(name, axis_pipeline, tmp_path):
+    """The two-field variants (both slots of a pair transformed by the same threads), forced through
+    the autotune cache: bitwise the single-field passes (the same arithmetic per line) and the oracle."""
+    import json
+    if name == "3d_kgauss64":
+        w = ti.small_workload("kgauss", 3, 64, 3, 30, n_tot=1e8, dt=DT_128)
+    elif name == "3d_kgauss64_odd":
+        w = ti.small_workload("kgauss", 3, 64, 4, 30, n_tot=1e8, dt=DT_128)      # 5 slots: a lone last slot
+    elif name == "2d_merger64":
+        w = ti.small_workload("merger2d", 2, 64, 5, 30, n_tot=1e9, dt=DT_2D)
+    else:
+        w = ti.small_workload("merger2d", 2, 2048, 2, 8, n_tot=1e9, dt=DT_2D)
+    cl = w.psi_cl()
+    out = []
+    for forced in (True, False):
+        path = str(tmp_path / f"force_dual{int(forced)}.json")
+        _force_dual(w, path, axis_pipeline, dual=forced)
+        ens = make_ensemble([w], 0)
+        ens.autotune(path)
+        if forced:
+            chosen = json.load(open(path))
+            n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)
+            key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
+            assert any(v & DUAL for k, v in chosen.items() if k.startswith(key) and ":op" in k)
+        ens.sample([cl], w.noise_seed)
+        ens.step(w.n_steps)
+        out.append(ens.fields(0).cpu().numpy().copy())
+        ens.close()
+    assert np.array_equal(out[0], out[1])
+    ref = oracle_batch(w, cl, w.n_steps)
+    assert np.all(field_rel_l2(out[0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
