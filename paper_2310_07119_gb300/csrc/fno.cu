@@ -24,6 +24,7 @@ void twa_set_global_error(const std::string& msg);
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kPwBlocks = 152 * 2;  // CTAs of the pointwise weight-gradient stage 1 (and its partials)
 
 int blocks_for(long long n) {
     const long long b = (n + kThreads - 1) / kThreads;
@@ -169,6 +170,186 @@ __global__ void k_mix_wgrad(const float2* __restrict__ G, const float2* __restri
         }
         dR[2 * t] += ar;
         dR[2 * t + 1] += ai;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Restructured contractions (same sums, same order per output; fewer passes over the inputs).
+
+// out[p][i][q] = sum_j M[i][j] in[p][j][q] (as k_axis): one thread per (p, q) and group of up to AG
+// outputs i, so every input value is read once per group; M is staged in shared memory and read
+// by the whole warp at the same address.
+constexpr int AG = 16;
+__global__ void k_axis_g(const float2* __restrict__ in_c, const float* __restrict__ in_r, const float2* __restrict__ M,
+                         float2* __restrict__ out_c, float* __restrict__ out_r, long long P, int nin, int nout, long long Q,
+                         int accumulate) {
+    extern __shared__ float2 Ms[];
+    for (int i = threadIdx.x; i < nin * nout; i += blockDim.x) Ms[i] = M[i];
+    __syncthreads();
+    const int ng = (nout + AG - 1) / AG;
+    const long long total = P * ng * Q;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long q = t % Q;
+        const long long r = t / Q;
+        const int g = (int)(r % ng);
+        const long long p = r / ng;
+        const int i0 = g * AG;
+        float ar[AG], ai[AG];
+#pragma unroll
+        for (int u = 0; u < AG; ++u) ar[u] = ai[u] = 0.f;
+        for (int j = 0; j < nin; ++j) {
+            const long long src = (p * nin + j) * Q + q;
+            if (in_r) {
+                const float x = in_r[src];
+#pragma unroll
+                for (int u = 0; u < AG; ++u) {
+                    const float2 m = Ms[min(i0 + u, nout - 1) * nin + j];
+                    ar[u] = fmaf(m.x, x, ar[u]);
+                    ai[u] = fmaf(m.y, x, ai[u]);
+                }
+            } else {
+                const float2 x = in_c[src];
+#pragma unroll
+                for (int u = 0; u < AG; ++u) {
+                    const float2 m = Ms[min(i0 + u, nout - 1) * nin + j];
+                    ar[u] = fmaf(m.x, x.x, fmaf(-m.y, x.y, ar[u]));
+                    ai[u] = fmaf(m.x, x.y, fmaf(m.y, x.x, ai[u]));
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < AG; ++u) {
+            const int i = i0 + u;
+            if (i >= nout) break;
+            const long long dst = (p * nout + i) * Q + q;
+            if (out_r) out_r[dst] = accumulate ? out_r[dst] + ar[u] : ar[u];
+            else out_c[dst] = make_float2(ar[u], ai[u]);
+        }
+    }
+}
+
+// k_mix with a CTA per block of MB modes: the modes' R matrices (W x W complex BF16) and the inputs
+// of every batch element for them are staged in shared memory, so R is read from memory once per
+// call instead of once per batch element.  Thread (x, mm): x = output channel (o, or c for ADJ).
+template <bool ADJ>
+__global__ void k_mix_g(const float2* __restrict__ S, const __nv_bfloat16* __restrict__ R, float2* __restrict__ Y, int B,
+                        int W, long long Mm, int MB) {
+    extern __shared__ float2 sm[];
+    float2* Rs = sm;                              // [MB][W][W]
+    float2* Ss = sm + (size_t)MB * W * W;         // [B][W][MB]
+    const int x = threadIdx.x % W, mm = threadIdx.x / W;
+    for (long long m0 = (long long)blockIdx.x * MB; m0 < Mm; m0 += (long long)gridDim.x * MB) {
+        const int nm = (int)min((long long)MB, Mm - m0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nm * W * W; i += blockDim.x) {
+            const long long ri = (m0 * W * W + i) * 2;
+            Rs[i] = make_float2(bf(R, ri), bf(R, ri + 1));
+        }
+        for (int i = threadIdx.x; i < B * W * MB; i += blockDim.x) {
+            const int k = i % MB, bc = i / MB;
+            Ss[i] = (k < nm) ? S[(long long)bc * Mm + m0 + k] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (mm < nm) {
+            for (int b = 0; b < B; ++b) {
+                float ar = 0.f, ai = 0.f;
+                for (int c = 0; c < W; ++c) {
+                    const float2 r = ADJ ? Rs[((size_t)mm * W + c) * W + x] : Rs[((size_t)mm * W + x) * W + c];
+                    const float rim = ADJ ? -r.y : r.y;
+                    const float2 v = Ss[((size_t)b * W + c) * MB + mm];
+                    ar = fmaf(r.x, v.x, fmaf(-rim, v.y, ar));
+                    ai = fmaf(r.x, v.y, fmaf(rim, v.x, ai));
+                }
+                Y[((long long)b * W + x) * Mm + m0 + mm] = make_float2(ar, ai);
+            }
+        }
+    }
+}
+
+// k_mix_wgrad with a CTA per block of MB modes: G and S of those modes staged in shared memory, one
+// thread per (o, c) pair of a mode, writes consecutive in c.
+__global__ void k_mix_wgrad_g(const float2* __restrict__ G, const float2* __restrict__ S, float* __restrict__ dR, int B,
+                              int W, long long Mm, int MB) {
+    extern __shared__ float2 sm[];
+    float2* Gs = sm;                         // [B][W][MB]
+    float2* Ss = sm + (size_t)B * W * MB;    // [B][W][MB]
+    for (long long m0 = (long long)blockIdx.x * MB; m0 < Mm; m0 += (long long)gridDim.x * MB) {
+        const int nm = (int)min((long long)MB, Mm - m0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < B * W * MB; i += blockDim.x) {
+            const int k = i % MB, bc = i / MB;
+            const bool in = k < nm;
+            Gs[i] = in ? G[(long long)bc * Mm + m0 + k] : make_float2(0.f, 0.f);
+            Ss[i] = in ? S[(long long)bc * Mm + m0 + k] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nm * W * W; i += blockDim.x) {
+            const int c = i % W, o = (i / W) % W, mm = i / (W * W);
+            float ar = 0.f, ai = 0.f;
+            for (int b = 0; b < B; ++b) {
+                const float2 g = Gs[((size_t)b * W + o) * MB + mm];
+                const float2 v = Ss[((size_t)b * W + c) * MB + mm];
+                ar = fmaf(g.x, v.x, fmaf(g.y, v.y, ar));
+                ai = fmaf(g.y, v.x, fmaf(-g.x, v.y, ai));
+            }
+            const long long t = (m0 + mm) * W * W + (long long)o * W + c;
+            dR[2 * t] += ar;
+            dR[2 * t + 1] += ai;
+        }
+    }
+}
+
+// Stage 1 of the pointwise weight gradient with a CTA per chunk of positions: dY and X of CH
+// positions staged in shared memory, each thread accumulating a few of the cout x (cin + 1) sums
+// over its CTA's chunks; part[(o * nblk + blk) * (cin + 1) + c] (stage 2 as before).
+constexpr int PW_CH = 64, PW_LD = PW_CH + 1;  // positions per chunk; padded row (distinct banks per channel)
+__global__ void k_pointwise_wgrad_g(const float* __restrict__ dY, const float* __restrict__ X, int B, int cin, int cout,
+                                    long long K, float* __restrict__ part) {
+    extern __shared__ float sm2[];
+    float* Ys = sm2;                         // [cout][PW_LD]
+    float* Xs = sm2 + (size_t)cout * PW_LD;  // [cin][PW_LD]
+    const int nout = cout * (cin + 1);
+    constexpr int MAXO = 8;
+    float acc[MAXO];
+#pragma unroll
+    for (int u = 0; u < MAXO; ++u) acc[u] = 0.f;
+    const long long kchunks = (K + PW_CH - 1) / PW_CH, total = (long long)B * kchunks;
+    for (long long ch = blockIdx.x; ch < total; ch += gridDim.x) {
+        const long long b = ch / kchunks, k0 = (ch % kchunks) * PW_CH;
+        const int nk = (int)min((long long)PW_CH, K - k0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cout * PW_CH; i += blockDim.x) {
+            const int o = i / PW_CH, k = i % PW_CH;
+            Ys[o * PW_LD + k] = k < nk ? dY[(b * cout + o) * K + k0 + k] : 0.f;
+        }
+        for (int i = threadIdx.x; i < cin * PW_CH; i += blockDim.x) {
+            const int c = i / PW_CH, k = i % PW_CH;
+            Xs[c * PW_LD + k] = k < nk ? X[(b * cin + c) * K + k0 + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < MAXO; ++u) {
+            const int j = threadIdx.x + u * blockDim.x;
+            if (j >= nout) break;
+            const int o = j / (cin + 1), c = j % (cin + 1);
+            const float* yr = Ys + (size_t)o * PW_LD;
+            float a = acc[u];
+            if (c < cin) {
+                const float* xr = Xs + (size_t)c * PW_LD;
+                for (int k = 0; k < PW_CH; ++k) a = fmaf(yr[k], xr[k], a);
+            } else {
+                for (int k = 0; k < PW_CH; ++k) a += yr[k];
+            }
+            acc[u] = a;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < MAXO; ++u) {
+        const int j = threadIdx.x + u * blockDim.x;
+        if (j >= nout) break;
+        const int o = j / (cin + 1), c = j % (cin + 1);
+        part[((long long)o * gridDim.x + blockIdx.x) * (cin + 1) + c] = acc[u];
     }
 }
 
@@ -338,6 +519,57 @@ int ensure_batch(twa_fno* f, int B) {
     return 0;
 }
 
+// Axis contraction: the grouped kernel when M fits in shared memory, else the per-output one.
+void axis_launch(const twa_fno* f, int blocks, int threads, int smem0, cudaStream_t st, const float2* in_c,
+                 const float* in_r, const float2* M, float2* out_c, float* out_r, long long P, int nin, int nout,
+                 long long Q, int accumulate) {
+    (void)f;
+    (void)smem0;
+    const size_t sm = (size_t)nin * nout * sizeof(float2);
+    if (sm <= 48 * 1024) {
+        const long long work = P * ((nout + AG - 1) / AG) * Q;
+        k_axis_g<<<blocks_for(work), threads, sm, st>>>(in_c, in_r, M, out_c, out_r, P, nin, nout, Q, accumulate);
+    } else {
+        k_axis<<<blocks, threads, 0, st>>>(in_c, in_r, M, out_c, out_r, P, nin, nout, Q, accumulate);
+    }
+}
+
+// Modes per CTA of the mixing kernels (W threads per mode) and their shared memory.
+int mix_modes(int W) { return kThreads / W > 0 ? kThreads / W : 1; }
+
+template <bool ADJ>
+void mix_launch(const float2* S, const __nv_bfloat16* R, float2* Y, int B, int W, long long Mm, cudaStream_t st) {
+    const int MB = mix_modes(W);
+    const size_t sm = ((size_t)MB * W * W + (size_t)B * W * MB) * sizeof(float2);
+    if (W <= kThreads && sm <= 100 * 1024) {
+        static size_t set = 0;
+        if (sm > set) {
+            cudaFuncSetAttribute(k_mix_g<ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            set = sm;
+        }
+        const long long nb = (Mm + MB - 1) / MB;
+        k_mix_g<ADJ><<<(int)(nb < 152LL * 8 ? nb : 152LL * 8), MB * W, sm, st>>>(S, R, Y, B, W, Mm, MB);
+    } else {
+        k_mix<ADJ><<<blocks_for((long long)B * W * Mm), kThreads, 0, st>>>(S, R, Y, B, W, Mm);
+    }
+}
+
+void mix_wgrad_launch(const float2* G, const float2* S, float* dR, int B, int W, long long Mm, cudaStream_t st) {
+    const int MB = mix_modes(W);
+    const size_t sm = (size_t)2 * B * W * MB * sizeof(float2);
+    if (sm <= 100 * 1024) {
+        static size_t set = 0;
+        if (sm > set) {
+            cudaFuncSetAttribute(k_mix_wgrad_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            set = sm;
+        }
+        const long long nb = (Mm + MB - 1) / MB;
+        k_mix_wgrad_g<<<(int)(nb < 152LL * 8 ? nb : 152LL * 8), kThreads, sm, st>>>(G, S, dR, B, W, Mm, MB);
+    } else {
+        k_mix_wgrad<<<blocks_for(Mm * W * W), kThreads, 0, st>>>(G, S, dR, B, W, Mm);
+    }
+}
+
 // A (truncated forward DFT) of a real [B*W][n][n][n] field into complex [B*W][2m][2m][2m].
 void dft_fwd(twa_fno* f, const float* in, float2* out, long long BW, cudaStream_t st) {
     const int n = f->cfg.grid, m2 = 2 * f->cfg.modes;
@@ -345,25 +577,25 @@ void dft_fwd(twa_fno* f, const float* in, float2* out, long long BW, cudaStream_
     if (!(f->tc_on && f->tc_fwd &&
           twa::tc_gemm(in, BW * n * n, n, n, f->Bf, 2 * m2, f->npf, reinterpret_cast<float*>(f->t1), 2 * m2, 0, f->d_err,
                   2.0, st) == 0))
-        k_axis<<<blocks_for(BW * n * n * m2), kThreads, 0, st>>>(nullptr, in, f->Mf[2], f->t1, nullptr, BW * n * n, n, m2, 1,
+        axis_launch(f, blocks_for(BW * n * n * m2), kThreads, 0, st, nullptr, in, f->Mf[2], f->t1, nullptr, BW * n * n, n, m2, 1,
                                                                   0);
     // y axis: (BW*n, n, 2m) -> (BW*n, 2m, 2m)
-    k_axis<<<blocks_for(BW * n * m2 * m2), kThreads, 0, st>>>(f->t1, nullptr, f->Mf[1], f->t2, nullptr, BW * n, n, m2, m2, 0);
+    axis_launch(f, blocks_for(BW * n * m2 * m2), kThreads, 0, st, f->t1, nullptr, f->Mf[1], f->t2, nullptr, BW * n, n, m2, m2, 0);
     // z axis: (BW, n, 4m^2) -> (BW, 2m, 4m^2)
-    k_axis<<<blocks_for(BW * m2 * m2 * m2), kThreads, 0, st>>>(f->t2, nullptr, f->Mf[0], out, nullptr, BW, n, m2,
+    axis_launch(f, blocks_for(BW * m2 * m2 * m2), kThreads, 0, st, f->t2, nullptr, f->Mf[0], out, nullptr, BW, n, m2,
                                                                (long long)m2 * m2, 0);
 }
 
 // Re A^H of complex [BW][2m][2m][2m] into a real [BW][n][n][n] field (overwrite or add).
 void dft_adj(twa_fno* f, const float2* in, float* out, long long BW, int accumulate, cudaStream_t st) {
     const int n = f->cfg.grid, m2 = 2 * f->cfg.modes;
-    k_axis<<<blocks_for(BW * n * m2 * m2), kThreads, 0, st>>>(in, nullptr, f->Mi[0], f->t1, nullptr, BW, m2, n,
+    axis_launch(f, blocks_for(BW * n * m2 * m2), kThreads, 0, st, in, nullptr, f->Mi[0], f->t1, nullptr, BW, m2, n,
                                                               (long long)m2 * m2, 0);
-    k_axis<<<blocks_for(BW * n * n * m2), kThreads, 0, st>>>(f->t1, nullptr, f->Mi[1], f->t2, nullptr, BW * n, m2, n, m2, 0);
+    axis_launch(f, blocks_for(BW * n * n * m2), kThreads, 0, st, f->t1, nullptr, f->Mi[1], f->t2, nullptr, BW * n, m2, n, m2, 0);
     if (!(f->tc_on && f->tc_adj &&
           twa::tc_gemm(reinterpret_cast<const float*>(f->t2), BW * n * n, 2 * m2, 2 * m2, f->Ba, n, f->npa, out, n, accumulate,
                   f->d_err, 2.0, st) == 0))
-        k_axis<<<blocks_for(BW * n * n * n), kThreads, 0, st>>>(f->t2, nullptr, f->Mi[2], nullptr, out, BW * n * n, m2, n,
+        axis_launch(f, blocks_for(BW * n * n * n), kThreads, 0, st, f->t2, nullptr, f->Mi[2], nullptr, out, BW * n * n, m2, n,
                                                                 1, accumulate);
 }
 
@@ -378,6 +610,13 @@ void pointwise(const float* X, const __nv_bfloat16* W, const float* b, float* Y,
 
 void pointwise_wgrad(twa_fno* f, const float* dY, const float* X, int B, int cin, int cout, long long K, float* dW,
                      float* db, cudaStream_t st) {
+    if ((long long)cout * (cin + 1) <= 8LL * kThreads) {
+        const int nblk = kPwBlocks;
+        const size_t sm = (size_t)(cin + cout) * PW_LD * sizeof(float);
+        k_pointwise_wgrad_g<<<nblk, kThreads, sm, st>>>(dY, X, B, cin, cout, K, f->part);
+        k_pointwise_wgrad_sum<<<(cout * (cin + 1) + 127) / 128, 128, 0, st>>>(f->part, cin, cout, nblk, dW, db);
+        return;
+    }
     const int nchunk = 64;
     k_pointwise_wgrad_part<<<dim3(cout, nchunk), kThreads, 0, st>>>(dY, X, B, cin, cout, K, nchunk, f->part);
     k_pointwise_wgrad_sum<<<(cout * (cin + 1) + 127) / 128, 128, 0, st>>>(f->part, cin, cout, nchunk, dW, db);
@@ -392,11 +631,11 @@ int twa_fno_create(twa_fno** out, const twa_fno_config* cfg, uint64_t seed) {
     if (!out || !cfg) return ffail(nullptr, TWA_EINVAL, "twa_fno_create: null argument");
     *out = nullptr;
     const twa_fno_config c = *cfg;
-    if (c.grid < 4 || c.grid > 64 || c.width < 1 || c.width > 64 || c.modes < 1 || 2 * c.modes > c.grid ||
+    if (c.grid < 4 || c.grid > 128 || c.width < 1 || c.width > 64 || c.modes < 1 || 2 * c.modes > c.grid ||
         c.layers < 1 || c.c_in < 1 || c.c_in > 64 || c.c_out < 1 || c.c_out > 64 ||
         2LL * (2 * c.modes) * (2 * c.modes) * (2 * c.modes) > (long long)c.grid * c.grid * c.grid)
         return ffail(nullptr, TWA_EINVAL,
-                     "twa_fno_create: sizes out of range (grid <= 64; width, c_in, c_out <= 64; 2 (2 modes)^3 <= grid^3)");
+                     "twa_fno_create: sizes out of range (grid <= 128; width, c_in, c_out <= 64; 2 (2 modes)^3 <= grid^3)");
     f = new twa_fno();
     f->cfg = c;
     const int W = c.width, L = c.layers;
@@ -421,7 +660,8 @@ int twa_fno_create(twa_fno** out, const twa_fno_config* cfg, uint64_t seed) {
         (rc = falloc(f, &f->am, o)) || (rc = falloc(f, &f->av, o)))
         return bail(rc);
     const int maxc = (W > c.c_in ? W : c.c_in) > c.c_out ? (W > c.c_in ? W : c.c_in) : c.c_out;
-    if ((rc = falloc(f, &f->part, (size_t)maxc * 64 * (maxc + 1))) || (rc = falloc(f, &f->lpart, (size_t)152 * 64)))
+    if ((rc = falloc(f, &f->part, (size_t)maxc * (kPwBlocks > 64 ? kPwBlocks : 64) * (maxc + 1))) ||
+        (rc = falloc(f, &f->lpart, (size_t)152 * 64)))
         return bail(rc);
     // truncated unitary DFT matrices (FP64 on the host), kept frequencies {0..m-1} U {n-m..n-1}
     const int n = c.grid, m2 = 2 * c.modes;
@@ -531,7 +771,7 @@ int twa_fno_forward(twa_fno* f, const float* x, int B, float* y, void* stream) {
     pointwise(x, P + f->oP, f->th + f->op, f->h[0], B, f->cfg.c_in, W, K, 0, false, st);
     for (int l = 0; l < L; ++l) {
         dft_fwd(f, f->h[l], f->s[l], BW, st);
-        k_mix<false><<<blocks_for(BW * Mm), kThreads, 0, st>>>(f->s[l], P + f->oR[l], f->mixed, B, W, Mm);
+        mix_launch<false>(f->s[l], P + f->oR[l], f->mixed, B, W, Mm, st);
         dft_adj(f, f->mixed, f->z[l], BW, 0, st);
         pointwise(f->h[l], P + f->oW[l], f->th + f->ob[l], f->z[l], B, W, W, K, 1, false, st);
         if (l < L - 1)
@@ -565,9 +805,8 @@ int twa_fno_backward(twa_fno* f, const float* dy, int B, float* dx, void* stream
         pointwise(dzl, P + f->oW[l], nullptr, f->dh2, B, W, W, K, 0, true, st);
         // spectral branch: dmixed = A dz, dR += dmixed conj(s), ds = R^H dmixed, dh += Re A^H ds
         dft_fwd(f, dzl, f->mixed, BW, st);
-        k_mix_wgrad<<<blocks_for(Mm * W * W), kThreads, 0, st>>>(f->mixed, f->s[l], g + f->oR[l], B, W, Mm);
-        k_mix<true><<<blocks_for(BW * Mm), kThreads, 0, st>>>(f->mixed, P + f->oR[l], reinterpret_cast<float2*>(f->dz),
-                                                               B, W, Mm);
+        mix_wgrad_launch(f->mixed, f->s[l], g + f->oR[l], B, W, Mm, st);
+        mix_launch<true>(f->mixed, P + f->oR[l], reinterpret_cast<float2*>(f->dz), B, W, Mm, st);
         // f->dz now holds ds (complex, B*W*Mm <= B*W*K floats / 2 since Mm <= K / 8)
         dft_adj(f, reinterpret_cast<float2*>(f->dz), f->dh2, BW, 1, st);
         std::swap(f->dh, f->dh2);
