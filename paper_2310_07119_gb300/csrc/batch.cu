@@ -30,10 +30,7 @@ __host__ __device__ constexpr int lines_of() { return kThreads / Plan<N>::T; }
 // Dynamic shared memory of one variant, as the stand-alone pass kernels size it.
 template <int N, bool STR, int OP>
 constexpr size_t smem_of() {
-    constexpr int L = lines_of<N>();
-    return ((size_t)L * (STR ? line_stride(N, L) : line_stride_rows(N, Plan<N>::T)) +
-            (op_stash(OP) ? (size_t)L * Plan<N>::T * Plan<N>::RMAX : 0)) * sizeof(float2) +
-           (size_t)smem_table_float4<N, OP>() * sizeof(float4);
+    return (size_t)TileSmem<N, lines_of<N>(), STR, OP, false>::total * sizeof(float2);
 }
 
 // One variant per (length, pass of the 2D pipeline), each compiled as a function of its own so its

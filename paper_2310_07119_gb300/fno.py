@@ -222,6 +222,35 @@ def correct_or_fallback(pred_corr: np.ndarray, est_corr: np.ndarray, grid: int, 
     return pred_corr, False
 
 
+def time_steps(grid: int, modes: int, batch: int, width: int = 32, layers: int = 4, reps: int = 3) -> dict:
+    """Device time of one training step (forward, MSE, backward, AdamW) and of one forward, with the
+    tensor-core GEMMs on and off, on random inputs (CUDA events on the current stream)."""
+    model = FNO(grid, width, modes, layers, seed=1)
+    lib = L.load()
+    x = torch.randn(batch, C_IN, grid, grid, grid, device=model.device)
+    t = torch.randn(batch, 1, grid, grid, grid, device=model.device)
+    out = {"grid": grid, "modes": modes, "batch": batch, "width": width, "layers": layers, "params": model.n_params,
+           "tensor_core_shapes": int(lib.twa_fno_tensor_core_shapes(model.h))}
+    for tc in (1, 0):
+        lib.twa_fno_set_tensor_cores(model.h, tc)
+        for _ in range(2):
+            model.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        for _ in range(reps):
+            model.train_step(x, t, 1e-4)
+        e[1].record()
+        e[2].record()
+        model.forward(x)
+        e[3].record()
+        torch.cuda.synchronize()
+        key = "tensor_cores" if tc else "cuda_cores"
+        out[key] = {"train_step_ms": e[0].elapsed_time(e[1]) / reps, "forward_ms": e[2].elapsed_time(e[3])}
+    model.close()
+    return out
+
+
 def main(argv=None):
     """Train the surrogate on library-generated runs and report held-out errors (JSON lines).
 
@@ -238,20 +267,32 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--width", type=int, default=32)
     ap.add_argument("--modes", type=int, default=6)
+    ap.add_argument("--k0", type=float, nargs=2, default=(2.0, 5.0), help="k0 range in units of 2 pi / L")
+    ap.add_argument("--snaps", type=int, nargs="+", default=None,
+                    help="snapshot steps (default: 150..400 at 32^3, scaled by (grid / 32)^2 so the times match)")
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--time", action="store_true", help="only time training steps (tensor cores on and off) and exit")
     a = ap.parse_args(argv)
+    if a.time:
+        print(json.dumps(time_steps(a.grid, a.modes, a.batch, a.width)))
+        return None
     grid = a.grid
     dt = ti.dt_pi4_rule(ti.Grid.cube(3, grid), ti.HBAR_3D)
-    snaps = [150, 200, 250, 300, 350, 400]
-    train_set = generate(run_table(a.runs, 1), grid, 8, 64, snaps, ti.HBAR_3D, ti.C_UNIT, dt)
+    snaps = a.snaps or [int(round(s * (grid / 32) ** 2)) for s in (150, 200, 250, 300, 350, 400)]
+    train_set = generate(run_table(a.runs, 1, k0_range=tuple(a.k0)), grid, 8, 64, snaps, ti.HBAR_3D, ti.C_UNIT, dt)
     # held-out reference: 1024 streams as two independent halves (their difference measures the
     # reference's own sampling noise)
     import twa_inputs as _ti
     g = _ti.Grid.cube(3, grid)
     rows = []
     model = FNO(grid, a.width, a.modes, 4, seed=3)
-    hist = train(model, train_set, a.iters, 8, a.lr, log_every=max(1, a.iters // 10))
+    import time
+    t0 = time.perf_counter()
+    hist = train(model, train_set, a.iters, a.batch, a.lr, log_every=max(1, a.iters // 10))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
     nb = grid // 2 - 2
-    for r in run_table(a.test_runs, 99):
+    for r in run_table(a.test_runs, 99, k0_range=tuple(a.k0)):
         psi_cl = _ti.kspace_gaussian(g, r["k0"] * 2.0 * np.pi, r["seed"])
         ens = Ensemble([g, g, g], ti.HBAR_3D, ti.C_UNIT, dt, r["n_tot"], [8, 512, 512], want_modes=True)
         ens.sample([psi_cl] * 3, r["seed"] + 1000003)
@@ -278,7 +319,8 @@ def main(argv=None):
         sel = [r for r in rows if r["step"] == s]
         summary[s] = {k: float(np.median([r[k] for r in sel])) for k in ("fno", "est8", "ref_noise")}
     print(json.dumps({"config": {"grid": grid, "width": a.width, "modes": a.modes, "layers": 4, "train_runs": a.runs,
-                                 "snapshots": snaps, "iters": a.iters, "params": model.n_params},
+                                 "snapshots": snaps, "iters": a.iters, "batch": a.batch, "params": model.n_params,
+                                 "k0": list(a.k0), "train_seconds": train_s},
                       "loss": hist, "median_shell_rel_err_vs_1024": summary}))
     return summary
 
