@@ -1833,7 +1833,12 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
     CU(cudaEventCreate(&e1));
     for (auto& I : h->in) {
         float2* f = inst_psi(I, psi);
-        const int Pn = I.n_pairs, Sn = I.n_slots;
+        // Each candidate is timed on a prefix of the pass's fields holding at least 8 GB (far above
+        // the L2), so the tuner's cost stays bounded on the largest batches (512^3 x 64 streams is
+        // 70 GB); every batch of up to 8 GB per pass is timed whole.
+        const long long unit = (long long)I.cells * (long long)sizeof(float2);
+        const long long cap = (8LL << 30) / unit + 1;
+        const int Pn = (int)std::min<long long>(I.n_pairs, cap), Sn = (int)std::min<long long>(I.n_slots, cap);
         std::vector<TunePass> passes;
         if (I.mode == MODE_1D) {
             passes = {{0, OP_STEPS_1D, Pn, I.vc, nullptr}};

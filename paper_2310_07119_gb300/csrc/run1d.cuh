@@ -22,48 +22,72 @@ struct Run1DArgs {
     double* part_bad; // [(n_out + 1) * n_pairs]: non-finite values met
 };
 
+// Each stream of a pair is a line of its own: the pair's two lines are neighbours in the CTA (lines
+// 2q and 2q + 1), T threads each, so the two fields' transforms run side by side (in one warp for
+// T <= 16) instead of one after the other, and each thread holds one field and the pair's packed
+// potential.  Both lines form the packed density (each takes the partner's |psi|^2 at the same
+// positions, by a shuffle or through shared memory) and transform it, so each has the potential
+// without a second exchange; the arithmetic of every field is that of the per-interval passes.
 template <int N, int LINES>
 __global__ void __launch_bounds__(LINES * Plan<N>::T, 1)
 k_run1d(const Run1DArgs r) {
+    static_assert(LINES % 2 == 0, "two lines per pair");
     using P = Plan<N>;
     constexpr int T = P::T, RMAX = P::RMAX;
     constexpr int LS = line_stride_rows(N, T);
     constexpr bool WARP = T <= 32;
+    constexpr bool SHFL = 2 * T <= 32;  // the pair's two lines share a warp
     constexpr unsigned MASK = (LINES * T >= 32) ? 0xffffffffu : ((1u << (LINES * T)) - 1u);
     extern __shared__ float2 smem[];
     const PassArgs& a = r.a;
     const int tid = threadIdx.x, l = tid / T, t = tid % T;
     float2* sm = smem + l * LS;
     const float4* tw = a.tw;
-    const int p = (int)blockIdx.x * LINES + l;
+    const int fld = l & 1;                                  // field of the pair on this line
+    const int p = ((int)blockIdx.x * LINES + l) >> 1;
     const bool active = p < a.n_pairs;
     const int pe = active ? p : a.n_pairs - 1;
-    const bool has1 = 2 * pe + 1 < a.n_slots;
-    float2* F0 = a.psi + (long long)(2 * pe) * N;
-    float2* F1 = a.psi + (long long)(2 * pe + 1) * N;
-    float2 v[RMAX], u[RMAX], w[RMAX];
+    const int slot = 2 * pe + fld;
+    const bool has = slot < a.n_slots;                      // the last pair of an odd slot count has one field
+    float2* F = a.psi + (long long)slot * N;                // dereferenced only when has
+    float2 v[RMAX], w[RMAX];
 #pragma unroll
-    for (int i = 0; i < RMAX; ++i) {
-        const int e = pos_nat<N>(t, i);
-        v[i] = F0[e];
-        u[i] = has1 ? F1[e] : make_float2(0.f, 0.f);
-    }
-    // (the two fields' transforms one after the other: interleaving them ran out of registers and
-    // measured slower, 1.27e9 against 1.48e9 cell-updates/s on the 256-cell workload)
-    auto drift = [&](float2 (&x)[RMAX]) {
-        fft_line<N, false, WARP, MASK>(x, t, sm, tw);
+    for (int i = 0; i < RMAX; ++i) v[i] = has ? F[pos_nat<N>(t, i)] : make_float2(0.f, 0.f);
+
+    // y = the partner line's x at this thread's positions (every thread of the CTA takes part)
+    auto swap_f = [&](const float (&x)[RMAX], float (&y)[RMAX]) {
+        if constexpr (SHFL) {
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) y[i] = __shfl_xor_sync(MASK, x[i], T);
+        } else {
+            float* mine = reinterpret_cast<float*>(sm);
+            const float* other = reinterpret_cast<const float*>(smem + (l ^ 1) * LS);
+            __syncthreads();  // the line regions are free of the last transform's exchange
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) mine[i * T + t] = x[i];
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) y[i] = other[i * T + t];
+            __syncthreads();  // before the next transform reuses the regions
+        }
+    };
+    auto drift = [&]() {
+        fft_line<N, false, WARP, MASK>(v, t, sm, tw);
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
             const float4 ph = __ldg(&a.ph[pos_spec<N>(t, i)]);
-            x[i] = cmul_c(x[i], make_float2(ph.x, ph.y), make_float2(ph.z, ph.w));
+            v[i] = cmul_c(v[i], make_float2(ph.x, ph.y), make_float2(ph.z, ph.w));
         }
-        fft_line<N, true, WARP, MASK>(x, t, sm, tw);
+        fft_line<N, true, WARP, MASK>(v, t, sm, tw);
     };
-    // packed potential of the pair: W = iFFT(FFT(|v|^2 + i |u|^2) / k^2)
+    // packed potential of the pair: W = iFFT(FFT(|psi_0|^2 + i |psi_1|^2) / k^2), on both lines
     auto poisson = [&]() {
+        float d[RMAX], e[RMAX];
 #pragma unroll
-        for (int i = 0; i < RMAX; ++i)
-            w[i] = make_float2(fmaf(v[i].x, v[i].x, v[i].y * v[i].y), fmaf(u[i].x, u[i].x, u[i].y * u[i].y));
+        for (int i = 0; i < RMAX; ++i) d[i] = fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
+        swap_f(d, e);
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) w[i] = fld ? make_float2(e[i], d[i]) : make_float2(d[i], e[i]);
         fft_line<N, false, WARP, MASK>(w, t, sm, tw);
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
@@ -72,80 +96,85 @@ k_run1d(const Run1DArgs r) {
         }
         fft_line<N, true, WARP, MASK>(w, t, sm, tw);
     };
-    // per-cell sums of the pair at output o; the pending half kick (hk != 0) applied to copies
+    auto pot = [&](int i) { return fld ? w[i].y : w[i].x; };
+    // per-cell sums of the pair at output o (the line of field 0 stores them); the pending half kick
+    // (hk != 0) applied to copies
     auto moments = [&](int o, float hk, float hk_lo) {
-        double* pp = r.part + ((long long)o * a.n_pairs + pe) * 3 * N;
+        float2 z[RMAX];
+        float x[RMAX], y[RMAX];
         int bad = 0;
+        const bool quantum = has && slot > 0;  // slot 0 is the classical field
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) {
-            if (!active) break;
-            const int e = pos_nat<N>(t, i);
-            // |psi|^2 does not depend on the pending kick (a phase): densities from the fields,
-            // the mean field from the kicked copies
-            const float2 z0 = hk != 0.f ? kick_w(v[i], hk, hk_lo, w[i].x) : v[i];
-            const float2 z1 = hk != 0.f ? kick_w(u[i], hk, hk_lo, w[i].y) : u[i];
-            double m2 = 0.0, pr = 0.0, pi = 0.0;
-            bad += (!isfinite(v[i].x) || !isfinite(v[i].y)) ? 1 : 0;
-            if (p > 0) {
-                m2 += (double)fmaf(v[i].x, v[i].x, v[i].y * v[i].y);
-                pr += (double)z0.x;
-                pi += (double)z0.y;
-            } else {
-                r.part_cl[(long long)o * N + e] = (double)v[i].x * v[i].x + (double)v[i].y * v[i].y;
-            }
-            if (has1) {
-                bad += (!isfinite(u[i].x) || !isfinite(u[i].y)) ? 1 : 0;
-                m2 += (double)fmaf(u[i].x, u[i].x, u[i].y * u[i].y);
-                pr += (double)z1.x;
-                pi += (double)z1.y;
-            }
-            pp[e] = m2;
-            pp[N + e] = pr;
-            pp[2 * N + e] = pi;
+            // |psi|^2 does not depend on the pending kick (a phase): densities from the field, the
+            // mean field from the kicked copy
+            z[i] = hk != 0.f ? kick_w(v[i], hk, hk_lo, pot(i)) : v[i];
+            bad += (has && (!isfinite(v[i].x) || !isfinite(v[i].y))) ? 1 : 0;
+            x[i] = quantum ? fmaf(v[i].x, v[i].x, v[i].y * v[i].y) : 0.f;
+            if (active && slot == 0)
+                r.part_cl[(long long)o * N + pos_nat<N>(t, i)] = (double)v[i].x * v[i].x + (double)v[i].y * v[i].y;
         }
-        // non-finite counts of the T threads of the line: a shuffle sum when the line sits in one warp,
-        // integer-valued atomic adds (exact, order-free) when it spans several
-        // (every lane takes part in the shuffles; lines past the last pair carry 0 and store nothing)
+        // the pair's sums in FP64 (the partner's float values, converted exactly)
+        double* pp = r.part + ((long long)o * a.n_pairs + pe) * 3 * N;
+        const bool store = active && fld == 0;
+        swap_f(x, y);
+        if (store) {
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) pp[pos_nat<N>(t, i)] = (double)x[i] + (double)y[i];
+        }
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) x[i] = quantum ? z[i].x : 0.f;
+        swap_f(x, y);
+        if (store) {
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) pp[N + pos_nat<N>(t, i)] = (double)x[i] + (double)y[i];
+        }
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) x[i] = quantum ? z[i].y : 0.f;
+        swap_f(x, y);
+        if (store) {
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) pp[2 * N + pos_nat<N>(t, i)] = (double)x[i] + (double)y[i];
+        }
+        // non-finite counts of the pair: a shuffle sum over each line, then over the two lines when
+        // they share a warp; otherwise integer-valued atomic adds (exact, order-free)
         if constexpr (T <= 32) {
 #pragma unroll
             for (int o2 = T / 2; o2 > 0; o2 >>= 1) bad += __shfl_down_sync(MASK, bad, o2, T);
-            if (active && t == 0) r.part_bad[(long long)o * a.n_pairs + p] = (double)bad;
+        }
+        if constexpr (SHFL) {
+            bad += __shfl_xor_sync(MASK, bad, T);
+            if (store && t == 0) r.part_bad[(long long)o * a.n_pairs + p] = (double)bad;
+        } else if (T <= 32) {
+            if (active && t == 0 && bad) atomicAdd(&r.part_bad[(long long)o * a.n_pairs + p], (double)bad);
         } else if (active && bad) {
             atomicAdd(&r.part_bad[(long long)o * a.n_pairs + p], (double)bad);
         }
     };
-    poisson();
-    if constexpr (T > 32) {
+    if constexpr (!SHFL) {
         // the bad-count slots of this launch start at zero (atomic adds)
         for (int o = 0; o <= r.n_out; ++o)
-            if (active && t == 0) r.part_bad[(long long)o * a.n_pairs + p] = 0.0;
+            if (active && fld == 0 && t == 0) r.part_bad[(long long)o * a.n_pairs + p] = 0.0;
         __syncthreads();
     }
+    poisson();
     moments(0, 0.f, 0.f);
 #pragma unroll 1
     for (int o = 1; o <= r.n_out; ++o) {
 #pragma unroll 1
         for (int s = 0; s < r.out_every; ++s) {
             const bool first = o == 1 && s == 0;
-            const float kk = first ? a.kick : a.kick2, kl = first ? a.kick_lo : a.kick2_lo;
-            kick_all(v, kk, kl, [&](int i) { return w[i].x; });
-            kick_all(u, kk, kl, [&](int i) { return w[i].y; });
-            drift(v);
-            drift(u);
+            kick_all(v, first ? a.kick : a.kick2, first ? a.kick_lo : a.kick2_lo, pot);
+            drift();
             poisson();
         }
         moments(o, a.kick, a.kick_lo);
     }
     // closing half kick: the batch ends synchronized
-    kick_all(v, a.kick, a.kick_lo, [&](int i) { return w[i].x; });
-    kick_all(u, a.kick, a.kick_lo, [&](int i) { return w[i].y; });
-    if (active) {
+    kick_all(v, a.kick, a.kick_lo, pot);
+    if (active && has) {
 #pragma unroll
-        for (int i = 0; i < RMAX; ++i) {
-            const int e = pos_nat<N>(t, i);
-            F0[e] = v[i];
-            if (has1) F1[e] = u[i];
-        }
+        for (int i = 0; i < RMAX; ++i) F[pos_nat<N>(t, i)] = v[i];
     }
 }
 

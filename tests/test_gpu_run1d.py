@@ -2,7 +2,9 @@
 
 On a handle whose instances are all 1D, twa_advance runs every step and the moment sums of every
 output on chip, one launch per instance plus one finishing launch (partial sums of the pairs in pair
-order).  With the pass profiler on, the same call runs the per-interval path (one on-chip launch per
+order).  Each stream is a line of its own; the two lines of a pair exchange densities and moment
+terms by shuffles (2T <= 32 threads) or through shared memory (T >= 32, lengths 512-2048), and both
+branches are covered by the lengths below.  With the pass profiler on, the same call runs the per-interval path (one on-chip launch per
 output interval and separate moment kernels).  The two do the same arithmetic per field, so the
 fields must be bitwise equal; the scalars add the streams in a different order and agree to
 rounding.  The series is also checked against the oracle's run (Sec. III.B.3, Eq. E[op], Eq. Q).
@@ -42,7 +44,7 @@ def _run(w, n_steps, every, fused, want_modes=True, poison=None):
     return out
 
 
-@pytest.mark.parametrize("n,n_real", [(8, 6), (256, 31), (256, 32), (2048, 5)])
+@pytest.mark.parametrize("n,n_real", [(8, 6), (16, 3), (64, 10), (256, 31), (256, 32), (512, 9), (1024, 4), (2048, 5)])
 def test_whole_run_equals_the_per_interval_path(n, n_real):
     w = ti.workload_1d_bump(n, n_real, 0)
     s_f, f_f, rc_f = _run(w, 60, 10, True)
