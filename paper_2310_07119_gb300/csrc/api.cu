@@ -111,7 +111,9 @@ struct twa_handle {
     bool fork = false;
     // run the steps of all instances as one persistent launch over a work list (2D batches)
     bool persist = false;
-    double wait_limit_s = 2.0;     // longest device-side wait of the persistent launch
+    double wait_limit_s = 2.0;     // longest device-side wait (persistent launch, TMA tile pipelines)
+    int clock_khz = 0;             // peak SM clock, converts the wait limit to clock64 cycles
+    std::map<std::string, CUtensorMap> tmaps;  // tensor maps of the TMA column passes, by buffer and shape
     bool stall_next = false;       // fault injection: the next persistent launch waits forever
     unsigned* d_ctr = nullptr;     // per-pair tile counters of the persistent launch
     unsigned long long* d_tick = nullptr;  // [0] ticket, [1] abort flag (low word)
@@ -238,6 +240,7 @@ int dispatch(int N, const LaunchCfg& c, const PassArgs& a, cudaStream_t st, bool
 
 constexpr int PIPE_FLAG = 1 << 16;  // "lines" values with this bit select the pipelined pass
 constexpr int DUAL_FLAG = 1 << 17;  // ... and with this bit the two-field variant (both slots of a pair)
+constexpr int TMA_FLAG = 1 << 18;   // ... and with PIPE_FLAG, the column pass whose tiles TMA copies
 
 int dispatch_pipe(int N, const LaunchCfg& c, const PassArgs& a, int tiles, int n_items, cudaStream_t st, bool prep) {
     switch (N) {
@@ -282,6 +285,13 @@ bool dual_variant_ok(int N, int op, bool strided, int lines) {
 
 bool variant_ok(int N, int op, bool strided, int lines) {
     if ((lines & PIPE_FLAG) && (lines & DUAL_FLAG)) return false;
+    if (lines & TMA_FLAG) {
+        // TMA tiles: column passes of the pipelined kernel; a box row of LINES 8-byte elements must
+        // span a multiple of 16 bytes
+        const int l = lines & ~(PIPE_FLAG | TMA_FLAG);
+        return (lines & PIPE_FLAG) && !(lines & DUAL_FLAG) && strided && l % 2 == 0 && encode_tiled_fn() &&
+               pipe_variant_ok(N, op, strided, l);
+    }
     if (lines & PIPE_FLAG) return pipe_variant_ok(N, op, strided, lines & ~PIPE_FLAG);
     if (lines & DUAL_FLAG) return dual_variant_ok(N, op, strided, lines & ~DUAL_FLAG);
     switch (N) {
@@ -345,7 +355,34 @@ PassArgs make_args(twa_handle* h, Inst& I, float2* psi, int axis, double kick_fr
     a.S = (int)stride;
     a.Qn = (int)stride;
     a.OS = stride * N;
+    a.err = h->d_err;
+    a.wait = (long long)(h->wait_limit_s * (double)h->clock_khz * 1e3);
     return a;
+}
+
+// Tensor map of `fields` fields of `cells` cells at base, for the TMA column passes along an axis of
+// N cells whose line starts are `stride` apart: a dense 4D tensor {line start, position, outer,
+// field} of 8-byte elements, boxes of `lines` line starts x min(N, 256) positions.
+const CUtensorMap* column_map(twa_handle* h, const float2* base, long long cells, int N, long long stride, int fields,
+                              int lines) {
+    std::ostringstream k;
+    k << (const void*)base << ":" << cells << ":" << N << ":" << stride << ":" << fields << ":" << lines;
+    auto it = h->tmaps.find(k.str());
+    if (it != h->tmaps.end()) return &it->second;
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return nullptr;
+    const cuuint64_t dims[4] = {(cuuint64_t)stride, (cuuint64_t)N, (cuuint64_t)(cells / (stride * N)),
+                                (cuuint64_t)fields};
+    const cuuint64_t strides[3] = {(cuuint64_t)stride * 8, (cuuint64_t)stride * N * 8, (cuuint64_t)cells * 8};
+    const cuuint32_t box[4] = {(cuuint32_t)lines, (cuuint32_t)std::min(N, 256), 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUtensorMap m;
+    if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<float2*>(base), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return nullptr;
+    if (h->tmaps.size() > 256) h->tmaps.clear();
+    return &(h->tmaps[k.str()] = m);
 }
 
 // One line pass over `fields` fields (pairs or slots) of instance I.
@@ -360,10 +397,11 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
     }
     const bool pipe = (lines & PIPE_FLAG) != 0;
     const bool dual = (lines & DUAL_FLAG) != 0;
+    const bool tma = (lines & TMA_FLAG) != 0;
     if (!variant_ok(N, op, strided, lines))
         return fail(h, TWA_EINVAL, "no pass variant for N=" + std::to_string(N) + " op=" + std::to_string(op) +
                                        " lines=" + std::to_string(lines));
-    lines &= ~(PIPE_FLAG | DUAL_FLAG);
+    lines &= ~(PIPE_FLAG | DUAL_FLAG | TMA_FLAG);
     // the two-field drift runs over pairs of slots
     const int slot_fields = fields;
     if (dual && op == OP_DRIFT) fields = (fields + 1) / 2;
@@ -374,6 +412,25 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
     c.strided = strided;
     c.lines = lines;
     c.dual = dual;
+    PipeMaps maps{};
+    if (tma) {
+        // the batch's fields (psi) and the pass's field buffer, as far as the op reads them
+        const bool reads_psi = op == OP_DRIFT || op == OP_DRIFT_RHO || op == OP_KICK_DRIFT || op == OP_KICK_DRIFT_VINV;
+        const bool reads_buf = op == OP_FWD || op == OP_INV || op == OP_FWD_MUL_INV || op == OP_KICK_DRIFT ||
+                               op == OP_KICK_DRIFT_VINV;
+        if (reads_psi) {
+            const CUtensorMap* m = column_map(h, psi, I.cells, N, stride, I.n_slots, lines);
+            if (!m) return fail(h, TWA_ECUDA, "cuTensorMapEncodeTiled failed");
+            maps.psi = *m;
+        }
+        if (reads_buf) {
+            const CUtensorMap* m = column_map(h, buf, I.cells, N, stride, fields, lines);
+            if (!m) return fail(h, TWA_ECUDA, "cuTensorMapEncodeTiled failed");
+            maps.buf = *m;
+        }
+        c.tma = true;
+        c.maps = &maps;
+    }
     if (op == OP_STEPS_1D) {
         c.grid = dim3((unsigned)((I.n_pairs + lines - 1) / lines), 1, 1);
     } else if (strided) {
@@ -392,7 +449,7 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
         if (lines_per_field % lines != 0 || (strided && stride % lines != 0))
             return fail(h, TWA_EINVAL, "pipelined pass needs full tiles");
     }
-    const long long pk = ((long long)dual << 42) | ((long long)pipe << 41) | ((long long)N << 24) |
+    const long long pk = ((long long)tma << 43) | ((long long)dual << 42) | ((long long)pipe << 41) | ((long long)N << 24) |
                          ((long long)op << 16) | ((long long)strided << 12) | lines;
     if (!h->prepared.count(pk)) {
         const int rc = pipe ? dispatch_pipe(N, c, a, tiles, n_items, st, true) : dispatch(N, c, a, st, true);
@@ -955,6 +1012,12 @@ int twa_create(twa_handle** out, const twa_grid* grids, const twa_params* p, int
         return code;
     };
     if ((rc = dalloc(h, &h->d_err, 1))) return bail(rc);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&h->clock_khz, cudaDevAttrClockRate, dev);
+        if (h->clock_khz <= 0) h->clock_khz = 2000000;
+    }
     if ((rc = dalloc(h, &h->d_vmax, (size_t)n_inst))) return bail(rc);
     if ((rc = dalloc(h, &h->d_counter, 1))) return bail(rc);
     if ((rc = dalloc(h, &h->d_cur, (size_t)n_inst * TWA_NSCALARS))) return bail(rc);
@@ -1512,7 +1575,7 @@ int twa_sync_status(twa_handle* h, void* stream) {
     CU(cudaMemcpy(&w, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     CU(cudaMemset(h->d_err, 0, sizeof(int)));
     if (w & TWA_ERR_TIMEOUT_BIT)
-        return fail(h, TWA_ETIMEOUT, "a device-side wait of the persistent batch launch gave up (wait limit " +
+        return fail(h, TWA_ETIMEOUT, "a device-side wait (persistent batch launch or TMA tile copy) gave up (wait limit " +
                                          std::to_string(h->wait_limit_s) + " s); the batch's fields are undefined");
     if (w & 1) return fail(h, TWA_ENONFINITE, "a moments pass met a non-finite field value");
     return TWA_OK;
@@ -1545,6 +1608,10 @@ int twa_set_wait_limit(twa_handle* h, double seconds) {
     if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
     if (!(seconds > 0.0) || seconds > 60.0) return fail(h, TWA_EINVAL, "twa_set_wait_limit: need 0 < seconds <= 60");
     h->wait_limit_s = seconds;
+    if (h->gexec) {  // captured launches carry the old limit
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
     return TWA_OK;
 }
 
@@ -1780,13 +1847,14 @@ int tune_passes(twa_handle* h, Inst& I, float2* f, const std::vector<TunePass>& 
                 cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
     const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512, PIPE_FLAG | 1, PIPE_FLAG | 2, PIPE_FLAG | 4,
                         PIPE_FLAG | 8, PIPE_FLAG | 16, PIPE_FLAG | 32, PIPE_FLAG | 64, DUAL_FLAG | 4, DUAL_FLAG | 8,
-                        DUAL_FLAG | 16, DUAL_FLAG | 32, DUAL_FLAG | 64, DUAL_FLAG | 128, DUAL_FLAG | 256};
+                        DUAL_FLAG | 16, DUAL_FLAG | 32, DUAL_FLAG | 64, DUAL_FLAG | 128, DUAL_FLAG | 256,
+                        PIPE_FLAG | TMA_FLAG | 4, PIPE_FLAG | TMA_FLAG | 8, PIPE_FLAG | TMA_FLAG | 16};
     for (const auto& ps : passes) {
         const int N = I.n[ps.axis == 3 ? 0 : ps.axis];
         auto ok = [&](int l) {
             if (ps.axis == 3) return (l & PIPE_FLAG) == 0 && plane_variant_ok(N, ps.op, l);
             if (!variant_ok(N, ps.op, ps.axis > 0, l)) return false;
-            const int ll = l & ~(PIPE_FLAG | DUAL_FLAG);
+            const int ll = l & ~(PIPE_FLAG | DUAL_FLAG | TMA_FLAG);
             if (l & PIPE_FLAG) {
                 long long stride = 1;
                 for (int b = 0; b < ps.axis; ++b) stride *= I.n[b];

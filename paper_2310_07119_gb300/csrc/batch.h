@@ -7,7 +7,6 @@
 namespace twa {
 
 constexpr int BATCH_THREADS = 256;       // threads of every CTA of the persistent launch (two per SM)
-constexpr int TWA_ERR_TIMEOUT_BIT = 2;   // device error word: a bounded wait gave up
 
 // One (step, pass, instance) entry of the work list.  Its items are tickets first .. first +
 // fields * items - 1; item r covers tiles [c * per_item, min((c + 1) * per_item, tiles)) of field

@@ -58,7 +58,11 @@ struct PassArgs {
     int nsteps;             // OP_STEPS_1D
     float post;             // OP_FWD: factor applied before the store (1, or 1/N to undo an inverse)
     const float4* ph2;      // plane passes: kinetic phase along y (hi, lo)
+    int* err;               // device error word (bit TWA_ERR_TIMEOUT_BIT: a bounded wait gave up)
+    long long wait;         // longest device-side wait, in clock64 cycles
 };
+
+constexpr int TWA_ERR_TIMEOUT_BIT = 2;  // device error word: a bounded wait gave up
 
 // Asks L2 to fetch a byte range ahead of its use (a hint: nothing waits on it, no data returns).
 // The range must lie inside one allocation, start on 16 bytes and span a multiple of 16 bytes.
@@ -675,6 +679,8 @@ struct LaunchCfg {
     int lines;
     dim3 grid;
     bool dual = false;  // two-field variant (both slots of a pair per thread; drift over pairs)
+    bool tma = false;   // pipelined column pass with TMA tile copies
+    const void* maps = nullptr;  // its tensor maps (PipeMaps, pipe.cuh)
 };
 template <int N>
 int launch_line(const LaunchCfg& c, const PassArgs& a, cudaStream_t st, bool prepare_only);

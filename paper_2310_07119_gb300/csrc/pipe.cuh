@@ -8,8 +8,18 @@
 // pipeline costs no extra shared memory beyond the second stage.  Results go straight from
 // registers to global memory.  Only full tiles are handled (the host checks that LINES divides the
 // line count); the per-thread arrays that live across the loads of one item sit in the stash.
+//
+// TMA variant (column passes): the tile is copied by the Tensor Memory Accelerator instead of the
+// threads' 16-byte copies.  The field is viewed as a dense 4D tensor {line start q, position j, outer
+// index, field} of 8-byte elements, and a tile (LINES consecutive line starts x N positions) is up
+// to eight boxes of LINES x 256 elements, issued by one thread and completed on the stage's
+// mbarrier.  The strided gathers (one 8 * LINES-byte segment per position) then cost the load/store
+// units nothing; the threads read the tile from shared memory in the same layout as the copies.
+// Every wait is bounded: on time-out the CTA sets TWA_ERR_TIMEOUT_BIT in the error word, lets its
+// copies in flight land (bounded) and returns.
 #pragma once
 #include "passes.cuh"
+#include "tma.cuh"
 
 namespace twa {
 
@@ -39,20 +49,43 @@ __host__ __device__ constexpr int pipe_stage_elems() {
     constexpr int raw = STRIDED ? LINES * N : LINES * line_stride_rows(N, T);
     return ((ex > raw ? ex : raw) + 1) / 2 * 2;
 }
+// stage elements rounded for the TMA variant (each stage starts on 128 bytes)
+template <int N, int LINES, bool STRIDED, bool TMA>
+__host__ __device__ constexpr int pipe_stage_elems_al() {
+    constexpr int se = pipe_stage_elems<N, LINES, STRIDED>();
+    return TMA ? (se + 15) / 16 * 16 : se;
+}
+// dynamic shared memory of a variant: two stages, the stash, and (TMA) 128 bytes of alignment slack
+template <int N, int LINES, bool STRIDED, int OP, bool TMA>
+__host__ __device__ constexpr size_t pipe_smem_bytes() {
+    return (2 * (size_t)pipe_stage_elems_al<N, LINES, STRIDED, TMA>() +
+            (pipe_stash(OP) ? (size_t)LINES * Plan<N>::T * Plan<N>::RMAX : 0)) * sizeof(float2) + (TMA ? 128 : 0);
+}
+// tensor maps of the TMA variant: the batch's fields and the pass's field buffer
+struct PipeMaps {
+    CUtensorMap psi;
+    CUtensorMap buf;
+};
 
-template <int N, int LINES, bool STRIDED, int OP>
+template <int N, int LINES, bool STRIDED, int OP, bool TMA>
 __global__ void __launch_bounds__(LINES * Plan<N>::T, min_ctas(LINES * Plan<N>::T))
-k_pipe(const PassArgs a, int tiles, int n_items) {
+k_pipe(const PassArgs a, int tiles, int n_items, const __grid_constant__ PipeMaps maps) {
+    static_assert(!TMA || STRIDED, "TMA tiles are for the column passes");
     using P = Plan<N>;
     constexpr int T = P::T, RMAX = P::RMAX, NTH = LINES * T;
     constexpr int LS = STRIDED ? line_stride(N, LINES) : line_stride_rows(N, T);
     constexpr int RS = line_stride_rows(N, T);      // row stride of a contiguous raw tile
     constexpr bool WARP = !STRIDED && (T <= 32);
     constexpr unsigned MASK = (NTH >= 32) ? 0xffffffffu : ((1u << NTH) - 1u);
-    constexpr int SE = pipe_stage_elems<N, LINES, STRIDED>();
+    constexpr int SE = pipe_stage_elems_al<N, LINES, STRIDED, TMA>();
     constexpr int LPI = pipe_loads(OP);
     constexpr int CHUNKS = LINES * N / 2;           // 16-byte copies per tile
-    extern __shared__ __align__(16) float2 psm[];
+    constexpr int BOXR = N < 256 ? N : 256;         // positions per TMA box
+    constexpr uint32_t TILE_BYTES = (uint32_t)LINES * N * sizeof(float2);
+    extern __shared__ __align__(16) float2 psm_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    float2* psm = psm_raw;
+    if constexpr (TMA) psm = psm_raw + (((128u - (smem_u32(psm_raw) & 127u)) & 127u) >> 3);
     float2* stage0 = psm;
     float2* stage1 = psm + SE;
     float* stf = reinterpret_cast<float*>(psm + 2 * SE) + threadIdx.x;  // per-thread stash, stf[i * NTH]
@@ -103,17 +136,79 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
         }
         cp_commit();
     };
-
-    if (Q > 0) issue(0);
-#pragma unroll 1
-    for (int q = 0; q < Q; ++q) {
-        if (q + 1 < Q) {
-            issue(q + 1);
-            cp_wait<1>();
+    // TMA: one thread copies the tile of load q into its stage; a missing slot only arrives
+    auto issue_tma = [&](int q) {
+        const int it = (int)blockIdx.x + (q / LPI) * G;
+        const int f = it / tiles, tile = it % tiles, sub = q % LPI;
+        const uint32_t bar = smem_u32(&bars[q & 1]);
+        const CUtensorMap* m = nullptr;
+        int fi = 0;
+        if constexpr (OP == OP_DRIFT) {
+            m = &maps.psi;
+            fi = f;
+        } else if constexpr (OP == OP_FWD || OP == OP_INV || OP == OP_FWD_MUL_INV) {
+            m = &maps.buf;
+            fi = f;
+        } else if constexpr (OP == OP_DRIFT_RHO) {
+            fi = 2 * f + sub;
+            if (fi < a.n_slots) m = &maps.psi;
         } else {
-            cp_wait<0>();
+            if (sub == 0) {
+                m = &maps.buf;
+                fi = f;
+            } else {
+                fi = 2 * f + sub - 1;
+                if (fi < a.n_slots) m = &maps.psi;
+            }
+        }
+        if (m) {
+            const uint32_t dst = smem_u32((q & 1) ? stage1 : stage0);
+            const int q0 = (tile % tq) * LINES, outer = tile / tq;
+            mbar_expect_tx(bar, TILE_BYTES);
+#pragma unroll
+            for (int b = 0; b < N / BOXR; ++b)
+                tma_load_4d(dst + (uint32_t)(b * BOXR * LINES * sizeof(float2)), m, q0, b * BOXR, outer, fi, bar);
+        } else {
+            mbar_arrive(bar);
+        }
+    };
+
+    if constexpr (TMA) {
+        if (tid == 0) {
+            mbar_init(smem_u32(&bars[0]), 1);
+            mbar_init(smem_u32(&bars[1]), 1);
+            mbar_init_fence();
         }
         __syncthreads();
+        if (Q > 0 && tid == 0) issue_tma(0);
+    } else {
+        if (Q > 0) issue(0);
+    }
+#pragma unroll 1
+    for (int q = 0; q < Q; ++q) {
+        if constexpr (TMA) {
+            if (q + 1 < Q && tid == 0) issue_tma(q + 1);
+            const bool ok = mbar_wait(smem_u32(&bars[q & 1]), (uint32_t)((q >> 1) & 1), a.wait);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicOr(a.err, TWA_ERR_TIMEOUT_BIT);
+                    // the copies in flight land before the CTA's shared memory is released
+                    mbar_wait(smem_u32(&bars[q & 1]), (uint32_t)((q >> 1) & 1), a.wait);
+                    if (q + 1 < Q)
+                        mbar_wait(smem_u32(&bars[(q + 1) & 1]), (uint32_t)(((q + 1) >> 1) & 1), a.wait);
+                }
+                __syncthreads();
+                return;
+            }
+        } else {
+            if (q + 1 < Q) {
+                issue(q + 1);
+                cp_wait<1>();
+            } else {
+                cp_wait<0>();
+            }
+            __syncthreads();
+        }
         const int it = (int)blockIdx.x + (q / LPI) * G;
         const int sub = q % LPI;
         const int f = it / tiles, tile = it % tiles;
@@ -222,6 +317,8 @@ k_pipe(const PassArgs a, int tiles, int n_items) {
                 }
             }
         }
+        // this item's shared-memory accesses precede the next TMA copy into its stage
+        if constexpr (TMA) fence_proxy_async_smem();
         __syncthreads();
     }
 }

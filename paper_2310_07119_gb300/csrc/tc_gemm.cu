@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "tc_gemm.h"
+#include "tma.cuh"
 
 namespace twa {
 namespace {
@@ -29,7 +30,6 @@ constexpr int BM = 128;           // rows per tile (MMA M)
 constexpr int ATOM_F = 32;        // floats per 128-byte swizzle row
 constexpr int THREADS = 128;
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor: 128-byte swizzle, K-major, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -47,33 +47,6 @@ __device__ __forceinline__ uint32_t idesc_tf32(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-// Wait for phase `parity` of the barrier for at most `budget` cycles; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget) {
-    const long long t0 = clock64();
-    for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > budget) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -118,14 +91,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
 
     if (threadIdx.x == 0) {
         s_fail = 0;
-        mbar_init(su32(&bar_a[0]), 1);
-        mbar_init(su32(&bar_a[1]), 1);
-        mbar_init(su32(&bar_b), 1);
-        mbar_init(su32(&bar_mma), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init(smem_u32(&bar_a[0]), 1);
+        mbar_init(smem_u32(&bar_a[1]), 1);
+        mbar_init(smem_u32(&bar_b), 1);
+        mbar_init(smem_u32(&bar_mma), 1);
+        mbar_init_fence();
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -137,13 +110,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     const uint32_t idesc = idesc_tf32(Np);
 
     auto load_a = [&](long long tile, int buf) {
-        mbar_expect_tx(su32(&bar_a[buf]), a_bytes);
+        mbar_expect_tx(smem_u32(&bar_a[buf]), a_bytes);
         for (int k = 0; k < natoms; ++k)
-            tma_load_2d(su32(sA[buf] + (size_t)k * BM * 128), &ta, k * ATOM_F, (int)(tile * BM), su32(&bar_a[buf]));
+            tma_load_2d(smem_u32(sA[buf] + (size_t)k * BM * 128), &ta, k * ATOM_F, (int)(tile * BM), smem_u32(&bar_a[buf]));
     };
     if (threadIdx.x == 0) {
-        mbar_expect_tx(su32(&bar_b), b_bytes);
-        for (int k = 0; k < natoms; ++k) tma_load_2d(su32(sB + (size_t)k * Np * 128), &tb, k * ATOM_F, 0, su32(&bar_b));
+        mbar_expect_tx(smem_u32(&bar_b), b_bytes);
+        for (int k = 0; k < natoms; ++k) tma_load_2d(smem_u32(sB + (size_t)k * Np * 128), &tb, k * ATOM_F, 0, smem_u32(&bar_b));
         if ((long long)blockIdx.x < ntiles) load_a(blockIdx.x, 0);
     }
     int issued = 0, used = 0;  // A tiles copied / consumed by this CTA (thread 0's count)
@@ -161,26 +134,26 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
                 ++issued;
             }
             bool ok = true;
-            if (i == 0) ok = b_done = mbar_wait(su32(&bar_b), 0, budget);
-            ok = ok && mbar_wait(su32(&bar_a[buf]), (uint32_t)((i >> 1) & 1), budget);
+            if (i == 0) ok = b_done = mbar_wait(smem_u32(&bar_b), 0, budget);
+            ok = ok && mbar_wait(smem_u32(&bar_a[buf]), (uint32_t)((i >> 1) & 1), budget);
             if (ok) {
                 ++used;
                 fence_after();
-                const uint32_t a0 = su32(sA[buf]), b0 = su32(sB);
+                const uint32_t a0 = smem_u32(sA[buf]), b0 = smem_u32(sB);
                 for (int s = 0; s < Kp / 8; ++s) {
                     const uint32_t koff = (uint32_t)(s % 4) * 32u;  // K = 8 TF32 values = 32 bytes
                     const uint64_t ad = sw128_desc(a0 + (uint32_t)(s / 4) * BM * 128 + koff);
                     const uint64_t bd = sw128_desc(b0 + (uint32_t)(s / 4) * (uint32_t)Np * 128 + koff);
                     mma_tf32(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
                 }
-                mma_commit(su32(&bar_mma));
+                mma_commit(smem_u32(&bar_mma));
             } else {
                 s_fail = 1;
             }
         }
         __syncthreads();
         if (s_fail) break;
-        if (!mbar_wait(su32(&bar_mma), (uint32_t)(i & 1), budget)) {
+        if (!mbar_wait(smem_u32(&bar_mma), (uint32_t)(i & 1), budget)) {
             atomicOr(&s_fail, 1);
         }
         __syncthreads();
@@ -218,8 +191,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     if (s_fail && threadIdx.x == 0) {
         atomicOr(err, TC_ERR_TIMEOUT_BIT);
         // copies still in flight land in this CTA's shared memory: wait for them (bounded) before leaving
-        for (int u = used; u < issued; ++u) mbar_wait(su32(&bar_a[u & 1]), (uint32_t)((u >> 1) & 1), budget);
-        if (!b_done) mbar_wait(su32(&bar_b), 0, budget);
+        for (int u = used; u < issued; ++u) mbar_wait(smem_u32(&bar_a[u & 1]), (uint32_t)((u >> 1) & 1), budget);
+        if (!b_done) mbar_wait(smem_u32(&bar_b), 0, budget);
     }
     fence_before();
     __syncthreads();
@@ -228,26 +201,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
 // 2D FP32 tensor map: rows of `inner` floats `stride_f` floats apart, boxes of 32 floats x box_rows.
 bool make_map(CUtensorMap* m, const float* base, long long inner, long long rows, long long stride_f, int box_rows) {
-    EncodeTiledFn fn = encode_fn();
+    EncodeTiledFn fn = encode_tiled_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)stride_f * sizeof(float)};

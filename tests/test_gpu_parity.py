@@ -437,3 +437,67 @@ def test_dual_passes_match_oracle_and_the_single_field_passes(name, axis_pipelin
     assert np.array_equal(out[0], out[1])
     ref = oracle_batch(w, cl, w.n_steps)
     assert np.all(field_rel_l2(out[0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
+
+
+TMA = 1 << 18      # with PIPE: the column pass whose tiles the Tensor Memory Accelerator copies
+COLUMN_OPS = (0, 3, 5, 6, 7)     # drift, drift_rho, fwd, fwd_mul_inv, inv
+
+
+def _force_columns(w, path, axis_pipeline, tma):
+    """Autotune cache that selects the pipelined variant of every column pass (y and z axes), with
+    TMA tile copies or with the threads' cp.async copies; the x passes are left to the tuner."""
+    import json
+    n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)
+    key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
+    cache = {f"{key}:axis9:op0": 0 if axis_pipeline else 1}
+    for ax in range(1, w.grid.dim):
+        lines = max(4, 128 // THREADS_PER_LINE[n[ax]])
+        for op in COLUMN_OPS:
+            cache[f"{key}:axis{ax}:op{op}"] = PIPE | (TMA if tma else 0) | lines
+    for op in (1, 2, 6):     # one fixed shape for the x passes, so both runs do the same arithmetic
+        cache[f"{key}:axis0:op{op}"] = max(1, 128 // THREADS_PER_LINE.get(n[0], 128))
+    json.dump(cache, open(path, "w"))
+
+
+@pytest.mark.parametrize("name,axis_pipeline", [("3d_kgauss64", True), ("3d_kgauss64_odd", True),
+                                                ("3d_kgauss64", False), ("2d_merger64", True), ("2d_merger512", True),
+                                                ("2d_merger2048", True)])
+def test_tma_column_passes_match_cp_async_and_oracle(name, axis_pipeline, tmp_path):
+    """The column passes with TMA tile copies (4D tensor maps over the batch, boxes of LINES x 256
+    elements, mbarrier completion) against the same passes fed by cp.async: the same values reach
+    the same shared-memory layout, so the fields are bitwise equal; and against the oracle.  The odd
+    case has a lone last slot (a stage with nothing to copy)."""
+    import json
+    from paper_2310_07119_gb300 import twa_sync_status
+    if name == "3d_kgauss64":
+        w = ti.small_workload("kgauss", 3, 64, 3, 20, n_tot=1e8, dt=DT_128)
+    elif name == "3d_kgauss64_odd":
+        w = ti.small_workload("kgauss", 3, 64, 4, 20, n_tot=1e8, dt=DT_128)
+    elif name == "2d_merger64":
+        w = ti.small_workload("merger2d", 2, 64, 5, 20, n_tot=1e9, dt=DT_2D)
+    elif name == "2d_merger512":
+        w = ti.small_workload("merger2d", 2, 512, 3, 10, n_tot=1e9, dt=DT_2D)
+    else:
+        w = ti.small_workload("merger2d", 2, 2048, 2, 6, n_tot=1e9, dt=DT_2D)
+    cl = w.psi_cl()
+    out = []
+    for tma in (True, False):
+        path = str(tmp_path / f"force_cols{int(tma)}.json")
+        _force_columns(w, path, axis_pipeline, tma)
+        ens = make_ensemble([w], 0)
+        ens.autotune(path)
+        chosen = json.load(open(path))
+        n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)
+        key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
+        for ax in range(1, w.grid.dim):
+            for op in COLUMN_OPS:
+                k = f"{key}:axis{ax}:op{op}"
+                assert chosen[k] & PIPE and bool(chosen[k] & TMA) == tma, (k, chosen[k])
+        ens.sample([cl], w.noise_seed)
+        ens.step(w.n_steps)
+        assert twa_sync_status(ens.h) == 0
+        out.append(ens.fields(0).cpu().numpy().copy())
+        ens.close()
+    assert np.array_equal(out[0], out[1])
+    ref = oracle_batch(w, cl, w.n_steps)
+    assert np.all(field_rel_l2(out[0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
