@@ -268,6 +268,19 @@ bool pipe_variant_ok(int N, int op, bool strided, int lines) {
     }
 }
 
+bool pipe_tma_variant_ok(int N, int op, int lines) {
+    switch (N) {
+        case 32: return has_pipe_tma_variant<32>(op, lines);
+        case 64: return has_pipe_tma_variant<64>(op, lines);
+        case 128: return has_pipe_tma_variant<128>(op, lines);
+        case 256: return has_pipe_tma_variant<256>(op, lines);
+        case 512: return has_pipe_tma_variant<512>(op, lines);
+        case 1024: return has_pipe_tma_variant<1024>(op, lines);
+        case 2048: return has_pipe_tma_variant<2048>(op, lines);
+        default: return false;
+    }
+}
+
 bool dual_variant_ok(int N, int op, bool strided, int lines) {
     switch (N) {
         case 8: return has_dual_variant<8>(op, strided, lines);
@@ -290,7 +303,7 @@ bool variant_ok(int N, int op, bool strided, int lines) {
         // span a multiple of 16 bytes
         const int l = lines & ~(PIPE_FLAG | TMA_FLAG);
         return (lines & PIPE_FLAG) && !(lines & DUAL_FLAG) && strided && l % 2 == 0 && encode_tiled_fn() &&
-               pipe_variant_ok(N, op, strided, l);
+               pipe_tma_variant_ok(N, op, l);
     }
     if (lines & PIPE_FLAG) return pipe_variant_ok(N, op, strided, lines & ~PIPE_FLAG);
     if (lines & DUAL_FLAG) return dual_variant_ok(N, op, strided, lines & ~DUAL_FLAG);
@@ -1848,7 +1861,8 @@ int tune_passes(twa_handle* h, Inst& I, float2* f, const std::vector<TunePass>& 
     const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512, PIPE_FLAG | 1, PIPE_FLAG | 2, PIPE_FLAG | 4,
                         PIPE_FLAG | 8, PIPE_FLAG | 16, PIPE_FLAG | 32, PIPE_FLAG | 64, DUAL_FLAG | 4, DUAL_FLAG | 8,
                         DUAL_FLAG | 16, DUAL_FLAG | 32, DUAL_FLAG | 64, DUAL_FLAG | 128, DUAL_FLAG | 256,
-                        PIPE_FLAG | TMA_FLAG | 4, PIPE_FLAG | TMA_FLAG | 8, PIPE_FLAG | TMA_FLAG | 16};
+                        PIPE_FLAG | TMA_FLAG | 2, PIPE_FLAG | TMA_FLAG | 4, PIPE_FLAG | TMA_FLAG | 8,
+                        PIPE_FLAG | TMA_FLAG | 16};
     for (const auto& ps : passes) {
         const int N = I.n[ps.axis == 3 ? 0 : ps.axis];
         auto ok = [&](int l) {

@@ -41,6 +41,10 @@ __host__ __device__ constexpr int pipe_loads(int op) {
     return (op == OP_KICK_DRIFT_VINV || op == OP_KICK_DRIFT) ? 3 : (op == OP_DRIFT_RHO ? 2 : 1);
 }
 __host__ __device__ constexpr bool pipe_stash(int op) { return pipe_loads(op) > 1; }
+// stash floats per thread: the first stream's density (drift_rho) or the pair's two potentials (kicks)
+__host__ __device__ constexpr int pipe_stash_floats(int op, int rmax) {
+    return !pipe_stash(op) ? 0 : (op == OP_DRIFT_RHO ? rmax : 2 * rmax);
+}
 // elements (float2) of one stage: the raw tile, or the padded exchange lines if larger
 template <int N, int LINES, bool STRIDED>
 __host__ __device__ constexpr int pipe_stage_elems() {
@@ -59,7 +63,7 @@ __host__ __device__ constexpr int pipe_stage_elems_al() {
 template <int N, int LINES, bool STRIDED, int OP, bool TMA>
 __host__ __device__ constexpr size_t pipe_smem_bytes() {
     return (2 * (size_t)pipe_stage_elems_al<N, LINES, STRIDED, TMA>() +
-            (pipe_stash(OP) ? (size_t)LINES * Plan<N>::T * Plan<N>::RMAX : 0)) * sizeof(float2) + (TMA ? 128 : 0);
+            (size_t)LINES * Plan<N>::T * pipe_stash_floats(OP, Plan<N>::RMAX) / 2) * sizeof(float2) + (TMA ? 128 : 0);
 }
 // tensor maps of the TMA variant: the batch's fields and the pass's field buffer
 struct PipeMaps {
@@ -327,5 +331,7 @@ template <int N>
 int launch_pipe(const LaunchCfg& c, const PassArgs& a, int tiles, int n_items, cudaStream_t st, bool prepare_only);
 template <int N>
 bool has_pipe_variant(int op, bool strided, int lines);
+template <int N>
+bool has_pipe_tma_variant(int op, int lines);
 
 }  // namespace twa

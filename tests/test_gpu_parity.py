@@ -443,15 +443,18 @@ TMA = 1 << 18      # with PIPE: the column pass whose tiles the Tensor Memory Ac
 COLUMN_OPS = (0, 3, 5, 6, 7)     # drift, drift_rho, fwd, fwd_mul_inv, inv
 
 
-def _force_columns(w, path, axis_pipeline, tma):
+def _force_columns(w, path, axis_pipeline, tma, narrow=False):
     """Autotune cache that selects the pipelined variant of every column pass (y and z axes), with
-    TMA tile copies or with the threads' cp.async copies; the x passes are left to the tuner."""
+    TMA tile copies or with the threads' cp.async copies (narrow: the TMA variant with two lines per
+    CTA, for lines of 64 or more threads); the x passes get one fixed shape."""
     import json
     n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)
     key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
     cache = {f"{key}:axis9:op0": 0 if axis_pipeline else 1}
     for ax in range(1, w.grid.dim):
         lines = max(4, 128 // THREADS_PER_LINE[n[ax]])
+        if narrow and tma and THREADS_PER_LINE[n[ax]] >= 64:
+            lines = 2
         for op in COLUMN_OPS:
             cache[f"{key}:axis{ax}:op{op}"] = PIPE | (TMA if tma else 0) | lines
     for op in (1, 2, 6):     # one fixed shape for the x passes, so both runs do the same arithmetic
@@ -461,7 +464,8 @@ def _force_columns(w, path, axis_pipeline, tma):
 
 @pytest.mark.parametrize("name,axis_pipeline", [("3d_kgauss64", True), ("3d_kgauss64_odd", True),
                                                 ("3d_kgauss64", False), ("2d_merger64", True), ("2d_merger512", True),
-                                                ("2d_merger2048", True)])
+                                                ("2d_merger2048", True), ("2d_merger2048_narrow", True),
+                                                ("2d_merger1024_narrow", True)])
 def test_tma_column_passes_match_cp_async_and_oracle(name, axis_pipeline, tmp_path):
     """The column passes with TMA tile copies (4D tensor maps over the batch, boxes of LINES x 256
     elements, mbarrier completion) against the same passes fed by cp.async: the same values reach
@@ -477,13 +481,16 @@ def test_tma_column_passes_match_cp_async_and_oracle(name, axis_pipeline, tmp_pa
         w = ti.small_workload("merger2d", 2, 64, 5, 20, n_tot=1e9, dt=DT_2D)
     elif name == "2d_merger512":
         w = ti.small_workload("merger2d", 2, 512, 3, 10, n_tot=1e9, dt=DT_2D)
+    elif name == "2d_merger1024_narrow":
+        w = ti.small_workload("merger2d", 2, 1024, 4, 8, n_tot=1e9, dt=DT_2D)
     else:
         w = ti.small_workload("merger2d", 2, 2048, 2, 6, n_tot=1e9, dt=DT_2D)
+    narrow = name.endswith("_narrow")
     cl = w.psi_cl()
     out = []
     for tma in (True, False):
         path = str(tmp_path / f"force_cols{int(tma)}.json")
-        _force_columns(w, path, axis_pipeline, tma)
+        _force_columns(w, path, axis_pipeline, tma, narrow)
         ens = make_ensemble([w], 0)
         ens.autotune(path)
         chosen = json.load(open(path))
