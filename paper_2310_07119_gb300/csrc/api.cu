@@ -268,15 +268,15 @@ bool pipe_variant_ok(int N, int op, bool strided, int lines) {
     }
 }
 
-bool pipe_tma_variant_ok(int N, int op, int lines) {
+bool pipe_tma_variant_ok(int N, int op, bool strided, int lines) {
     switch (N) {
-        case 32: return has_pipe_tma_variant<32>(op, lines);
-        case 64: return has_pipe_tma_variant<64>(op, lines);
-        case 128: return has_pipe_tma_variant<128>(op, lines);
-        case 256: return has_pipe_tma_variant<256>(op, lines);
-        case 512: return has_pipe_tma_variant<512>(op, lines);
-        case 1024: return has_pipe_tma_variant<1024>(op, lines);
-        case 2048: return has_pipe_tma_variant<2048>(op, lines);
+        case 32: return has_pipe_tma_variant<32>(op, strided, lines);
+        case 64: return has_pipe_tma_variant<64>(op, strided, lines);
+        case 128: return has_pipe_tma_variant<128>(op, strided, lines);
+        case 256: return has_pipe_tma_variant<256>(op, strided, lines);
+        case 512: return has_pipe_tma_variant<512>(op, strided, lines);
+        case 1024: return has_pipe_tma_variant<1024>(op, strided, lines);
+        case 2048: return has_pipe_tma_variant<2048>(op, strided, lines);
         default: return false;
     }
 }
@@ -299,11 +299,12 @@ bool dual_variant_ok(int N, int op, bool strided, int lines) {
 bool variant_ok(int N, int op, bool strided, int lines) {
     if ((lines & PIPE_FLAG) && (lines & DUAL_FLAG)) return false;
     if (lines & TMA_FLAG) {
-        // TMA tiles: column passes of the pipelined kernel; a box row of LINES 8-byte elements must
-        // span a multiple of 16 bytes
+        // TMA tiles of the pipelined kernel: column tiles by tensor map (a box row of LINES 8-byte
+        // elements must span a multiple of 16 bytes), row tiles by one bulk copy per row
         const int l = lines & ~(PIPE_FLAG | TMA_FLAG);
-        return (lines & PIPE_FLAG) && !(lines & DUAL_FLAG) && strided && l % 2 == 0 && encode_tiled_fn() &&
-               pipe_tma_variant_ok(N, op, l);
+        if (!(lines & PIPE_FLAG) || (lines & DUAL_FLAG)) return false;
+        if (strided) return l % 2 == 0 && encode_tiled_fn() && pipe_tma_variant_ok(N, op, true, l);
+        return pipe_tma_variant_ok(N, op, false, l);
     }
     if (lines & PIPE_FLAG) return pipe_variant_ok(N, op, strided, lines & ~PIPE_FLAG);
     if (lines & DUAL_FLAG) return dual_variant_ok(N, op, strided, lines & ~DUAL_FLAG);
@@ -426,7 +427,7 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
     c.lines = lines;
     c.dual = dual;
     PipeMaps maps{};
-    if (tma) {
+    if (tma && strided) {
         // the batch's fields (psi) and the pass's field buffer, as far as the op reads them
         const bool reads_psi = op == OP_DRIFT || op == OP_DRIFT_RHO || op == OP_KICK_DRIFT || op == OP_KICK_DRIFT_VINV;
         const bool reads_buf = op == OP_FWD || op == OP_INV || op == OP_FWD_MUL_INV || op == OP_KICK_DRIFT ||
@@ -441,9 +442,9 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
             if (!m) return fail(h, TWA_ECUDA, "cuTensorMapEncodeTiled failed");
             maps.buf = *m;
         }
-        c.tma = true;
         c.maps = &maps;
     }
+    c.tma = tma;
     if (op == OP_STEPS_1D) {
         c.grid = dim3((unsigned)((I.n_pairs + lines - 1) / lines), 1, 1);
     } else if (strided) {
@@ -1861,8 +1862,9 @@ int tune_passes(twa_handle* h, Inst& I, float2* f, const std::vector<TunePass>& 
     const int cand[] = {1, 2, 4, 8, 16, 32, 64, 128, 256, 512, PIPE_FLAG | 1, PIPE_FLAG | 2, PIPE_FLAG | 4,
                         PIPE_FLAG | 8, PIPE_FLAG | 16, PIPE_FLAG | 32, PIPE_FLAG | 64, DUAL_FLAG | 4, DUAL_FLAG | 8,
                         DUAL_FLAG | 16, DUAL_FLAG | 32, DUAL_FLAG | 64, DUAL_FLAG | 128, DUAL_FLAG | 256,
-                        PIPE_FLAG | TMA_FLAG | 2, PIPE_FLAG | TMA_FLAG | 4, PIPE_FLAG | TMA_FLAG | 8,
-                        PIPE_FLAG | TMA_FLAG | 16};
+                        PIPE_FLAG | TMA_FLAG | 1, PIPE_FLAG | TMA_FLAG | 2, PIPE_FLAG | TMA_FLAG | 4,
+                        PIPE_FLAG | TMA_FLAG | 8, PIPE_FLAG | TMA_FLAG | 16, PIPE_FLAG | TMA_FLAG | 32,
+                        PIPE_FLAG | TMA_FLAG | 64};
     for (const auto& ps : passes) {
         const int N = I.n[ps.axis == 3 ? 0 : ps.axis];
         auto ok = [&](int l) {

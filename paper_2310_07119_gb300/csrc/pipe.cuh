@@ -15,6 +15,8 @@
 // to eight boxes of LINES x 256 elements, issued by one thread and completed on the stage's
 // mbarrier.  The strided gathers (one 8 * LINES-byte segment per position) then cost the load/store
 // units nothing; the threads read the tile from shared memory in the same layout as the copies.
+// Row passes take the same path with one bulk copy (cp.async.bulk) per contiguous row into the
+// padded stage rows.
 // Every wait is bounded: on time-out the CTA sets TWA_ERR_TIMEOUT_BIT in the error word, lets its
 // copies in flight land (bounded) and returns.
 #pragma once
@@ -74,7 +76,6 @@ struct PipeMaps {
 template <int N, int LINES, bool STRIDED, int OP, bool TMA>
 __global__ void __launch_bounds__(LINES * Plan<N>::T, min_ctas(LINES * Plan<N>::T))
 k_pipe(const PassArgs a, int tiles, int n_items, const __grid_constant__ PipeMaps maps) {
-    static_assert(!TMA || STRIDED, "TMA tiles are for the column passes");
     using P = Plan<N>;
     constexpr int T = P::T, RMAX = P::RMAX, NTH = LINES * T;
     constexpr int LS = STRIDED ? line_stride(N, LINES) : line_stride_rows(N, T);
@@ -86,6 +87,7 @@ k_pipe(const PassArgs a, int tiles, int n_items, const __grid_constant__ PipeMap
     constexpr int CHUNKS = LINES * N / 2;           // 16-byte copies per tile
     constexpr int BOXR = N < 256 ? N : 256;         // positions per TMA box
     constexpr uint32_t TILE_BYTES = (uint32_t)LINES * N * sizeof(float2);
+    static_assert(!TMA || STRIDED || RS % 2 == 0, "bulk row copies need 16-byte aligned shared rows");
     extern __shared__ __align__(16) float2 psm_raw[];
     __shared__ __align__(8) uint64_t bars[2];
     float2* psm = psm_raw;
@@ -165,7 +167,21 @@ k_pipe(const PassArgs a, int tiles, int n_items, const __grid_constant__ PipeMap
                 if (fi < a.n_slots) m = &maps.psi;
             }
         }
-        if (m) {
+        if constexpr (!STRIDED) {
+            // row tiles: LINES contiguous rows, one bulk copy each into the padded stage rows
+            const float2* src = source(f, sub);
+            if (src) {
+                const uint32_t dst = smem_u32((q & 1) ? stage1 : stage0);
+                const float2* s0 = src + tile_base(tile);
+                mbar_expect_tx(bar, TILE_BYTES);
+#pragma unroll 1
+                for (int r = 0; r < LINES; ++r)
+                    bulk_load(dst + (uint32_t)(r * RS * sizeof(float2)), s0 + (long long)r * N,
+                              (uint32_t)(N * sizeof(float2)), bar);
+            } else {
+                mbar_arrive(bar);
+            }
+        } else if (m) {
             const uint32_t dst = smem_u32((q & 1) ? stage1 : stage0);
             const int q0 = (tile % tq) * LINES, outer = tile / tq;
             mbar_expect_tx(bar, TILE_BYTES);
@@ -332,6 +348,6 @@ int launch_pipe(const LaunchCfg& c, const PassArgs& a, int tiles, int n_items, c
 template <int N>
 bool has_pipe_variant(int op, bool strided, int lines);
 template <int N>
-bool has_pipe_tma_variant(int op, int lines);
+bool has_pipe_tma_variant(int op, bool strided, int lines);
 
 }  // namespace twa

@@ -508,3 +508,62 @@ def test_tma_column_passes_match_cp_async_and_oracle(name, axis_pipeline, tmp_pa
     assert np.array_equal(out[0], out[1])
     ref = oracle_batch(w, cl, w.n_steps)
     assert np.all(field_rel_l2(out[0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
+
+
+ROW_OPS = (1, 2, 5, 6, 7)     # kick_drift, kick_drift_vinv, fwd, fwd_mul_inv, inv
+
+
+def _force_rows(w, path, axis_pipeline, tma):
+    """Autotune cache that selects the pipelined variant of every row pass (x axis), its tiles copied
+    by one bulk copy per row (TMA) or by the threads' cp.async copies; other passes get fixed shapes."""
+    import json
+    n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)
+    key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
+    cache = {f"{key}:axis9:op0": 0 if axis_pipeline else 1}
+    lines = max(1, 128 // THREADS_PER_LINE[n[0]])
+    for op in ROW_OPS:
+        cache[f"{key}:axis0:op{op}"] = PIPE | (TMA if tma else 0) | lines
+    for ax in range(1, w.grid.dim):
+        for op in COLUMN_OPS:
+            cache[f"{key}:axis{ax}:op{op}"] = max(4, 128 // THREADS_PER_LINE[n[ax]])
+    json.dump(cache, open(path, "w"))
+
+
+@pytest.mark.parametrize("name,axis_pipeline", [("3d_kgauss64", True), ("3d_kgauss64_odd", True),
+                                                ("2d_merger64", True), ("2d_merger512", True),
+                                                ("2d_merger2048", True)])
+def test_tma_row_passes_match_cp_async_and_oracle(name, axis_pipeline, tmp_path):
+    """The row passes with their tiles moved by bulk copies (cp.async.bulk, one per row, completion
+    on the stage's mbarrier) against the same passes fed by cp.async (bitwise) and the oracle."""
+    import json
+    from paper_2310_07119_gb300 import twa_sync_status
+    if name == "3d_kgauss64":
+        w = ti.small_workload("kgauss", 3, 64, 3, 20, n_tot=1e8, dt=DT_128)
+    elif name == "3d_kgauss64_odd":
+        w = ti.small_workload("kgauss", 3, 64, 4, 20, n_tot=1e8, dt=DT_128)
+    elif name == "2d_merger64":
+        w = ti.small_workload("merger2d", 2, 64, 5, 20, n_tot=1e9, dt=DT_2D)
+    elif name == "2d_merger512":
+        w = ti.small_workload("merger2d", 2, 512, 3, 10, n_tot=1e9, dt=DT_2D)
+    else:
+        w = ti.small_workload("merger2d", 2, 2048, 2, 6, n_tot=1e9, dt=DT_2D)
+    cl = w.psi_cl()
+    out = []
+    for tma in (True, False):
+        path = str(tmp_path / f"force_rows{int(tma)}.json")
+        _force_rows(w, path, axis_pipeline, tma)
+        ens = make_ensemble([w], 0)
+        ens.autotune(path)
+        chosen = json.load(open(path))
+        n = list(w.grid.shape[::-1]) + [1] * (3 - w.grid.dim)
+        key = f"{n[0]}x{n[1]}x{n[2]}:slots{w.n_real + 1}"
+        used = [k for k in chosen if k.startswith(f"{key}:axis0:") and int(k.rsplit("op", 1)[1]) in ROW_OPS]
+        assert used and all(bool(chosen[k] & TMA) == tma and chosen[k] & PIPE for k in used), chosen
+        ens.sample([cl], w.noise_seed)
+        ens.step(w.n_steps)
+        assert twa_sync_status(ens.h) == 0
+        out.append(ens.fields(0).cpu().numpy().copy())
+        ens.close()
+    assert np.array_equal(out[0], out[1])
+    ref = oracle_batch(w, cl, w.n_steps)
+    assert np.all(field_rel_l2(out[0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
