@@ -316,8 +316,9 @@ int twa_sync_status(twa_handle* h, void* stream);
 int twa_set_batch_mode(twa_handle* h, int mode);
 int twa_get_batch_mode(const twa_handle* h);
 
-/* Longest time a CTA of the persistent launch waits for a dependency before it gives up (default 2 s,
-   0 < seconds <= 60; counted in SM clock cycles at the device's peak clock). */
+/* Longest time a CTA of the persistent launch waits for a dependency, or a CTA of a TMA tile pass for
+   its tile, before it gives up (default 2 s, 0 < seconds <= 60; counted in SM clock cycles at the
+   device's peak clock). */
 int twa_set_wait_limit(twa_handle* h, double seconds);
 
 /* Fault injection for tests of the failure path: the next persistent launch of this handle waits for
@@ -325,6 +326,13 @@ int twa_set_wait_limit(twa_handle* h, double seconds);
    twa_sync_status reports TWA_ETIMEOUT.  Nothing faults: the GPU stays usable and later calls run
    normally.  TWA_EINVAL if the handle has no persistent launch. */
 int twa_debug_stall_next_batch(twa_handle* h);
+
+/* Fault injection for tests of the failure path of the TMA tile pipelines: the next pass that runs a
+   TMA variant (eagerly, outside a graph capture) expects 16 bytes per tile more than its copies
+   deliver, so its CTAs' waits run out after the wait limit, the pass stops (the fields it was to
+   update are undefined) and twa_sync_status reports TWA_ETIMEOUT.  Nothing faults: the GPU stays
+   usable and later calls run normally.  TWA_EINVAL for an FP64 handle. */
+int twa_debug_stall_next_tma(twa_handle* h);
 
 /* Message of the last failure on this handle (or of the last twa_create failure if h is NULL). */
 const char* twa_last_error(const twa_handle* h);

@@ -68,6 +68,7 @@ _SIGS = {
     "twa_get_batch_mode": (ctypes.c_int, [_P]),
     "twa_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_double]),
     "twa_debug_stall_next_batch": (ctypes.c_int, [_P]),
+    "twa_debug_stall_next_tma": (ctypes.c_int, [_P]),
     "twa_last_error": (ctypes.c_char_p, [_P]),
     "twa_autotune": (ctypes.c_int, [_P, _P, ctypes.c_char_p, _P]),
     "twa_last_launch_count": (ctypes.c_longlong, [_P]),

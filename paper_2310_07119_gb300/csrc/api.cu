@@ -115,6 +115,7 @@ struct twa_handle {
     int clock_khz = 0;             // peak SM clock, converts the wait limit to clock64 cycles
     std::map<std::string, CUtensorMap> tmaps;  // tensor maps of the TMA column passes, by buffer and shape
     bool stall_next = false;       // fault injection: the next persistent launch waits forever
+    bool stall_tma = false;        // fault injection: the next TMA tile pass expects bytes that never come
     unsigned* d_ctr = nullptr;     // per-pair tile counters of the persistent launch
     unsigned long long* d_tick = nullptr;  // [0] ticket, [1] abort flag (low word)
     struct BatchTable {
@@ -419,7 +420,15 @@ int run_pass(twa_handle* h, Inst& I, float2* psi, int axis, int op, double kick_
     // the two-field drift runs over pairs of slots
     const int slot_fields = fields;
     if (dual && op == OP_DRIFT) fields = (fields + 1) / 2;
-    const PassArgs a = make_args(h, I, psi, axis, kick_frac, buf, out, nsteps, post);
+    PassArgs a = make_args(h, I, psi, axis, kick_frac, buf, out, nsteps, post);
+    if (tma && h->stall_tma) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs == cudaStreamCaptureStatusNone) {  // never baked into a graph
+            a.stall_tx = 16;
+            h->stall_tma = false;
+        }
+    }
     const long long stride = a.S;
     LaunchCfg c{};
     c.op = op;
@@ -1626,6 +1635,13 @@ int twa_set_wait_limit(twa_handle* h, double seconds) {
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
     }
+    return TWA_OK;
+}
+
+int twa_debug_stall_next_tma(twa_handle* h) {
+    if (!h) return fail(nullptr, TWA_EINVAL, "null handle");
+    if (h->p.precision != TWA_F32) return fail(h, TWA_EINVAL, "twa_debug_stall_next_tma: FP32 handles only");
+    h->stall_tma = true;
     return TWA_OK;
 }
 

@@ -60,6 +60,7 @@ struct PassArgs {
     const float4* ph2;      // plane passes: kinetic phase along y (hi, lo)
     int* err;               // device error word (bit TWA_ERR_TIMEOUT_BIT: a bounded wait gave up)
     long long wait;         // longest device-side wait, in clock64 cycles
+    unsigned stall_tx;      // fault injection (tests): bytes a TMA tile pass expects beyond its copies
 };
 
 constexpr int TWA_ERR_TIMEOUT_BIT = 2;  // device error word: a bounded wait gave up

@@ -173,7 +173,7 @@ k_pipe(const PassArgs a, int tiles, int n_items, const __grid_constant__ PipeMap
             if (src) {
                 const uint32_t dst = smem_u32((q & 1) ? stage1 : stage0);
                 const float2* s0 = src + tile_base(tile);
-                mbar_expect_tx(bar, TILE_BYTES);
+                mbar_expect_tx(bar, TILE_BYTES + a.stall_tx);
 #pragma unroll 1
                 for (int r = 0; r < LINES; ++r)
                     bulk_load(dst + (uint32_t)(r * RS * sizeof(float2)), s0 + (long long)r * N,
@@ -184,7 +184,7 @@ k_pipe(const PassArgs a, int tiles, int n_items, const __grid_constant__ PipeMap
         } else if (m) {
             const uint32_t dst = smem_u32((q & 1) ? stage1 : stage0);
             const int q0 = (tile % tq) * LINES, outer = tile / tq;
-            mbar_expect_tx(bar, TILE_BYTES);
+            mbar_expect_tx(bar, TILE_BYTES + a.stall_tx);
 #pragma unroll
             for (int b = 0; b < N / BOXR; ++b)
                 tma_load_4d(dst + (uint32_t)(b * BOXR * LINES * sizeof(float2)), m, q0, b * BOXR, outer, fi, bar);

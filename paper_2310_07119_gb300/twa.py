@@ -20,7 +20,7 @@ __all__ = [
     "twa_last_launch_count", "twa_poisson_multiplier", "twa_observable_create", "twa_observable_eval",
     "twa_observable_destroy", "Observable", "twa_advance", "twa_advance_adaptive", "twa_phase_moments", "twa_particles_set", "twa_particles_get", "twa_profile_enable", "twa_profile_read", "Ensemble", "F32",
     "F64_PLAIN", "SCALAR_NAMES", "PASS_NAMES", "twa_set_batch_mode", "twa_get_batch_mode", "twa_set_wait_limit",
-    "twa_debug_stall_next_batch", "BATCH_SERIAL", "BATCH_FORK", "BATCH_PERSISTENT",
+    "twa_debug_stall_next_batch", "twa_debug_stall_next_tma", "BATCH_SERIAL", "BATCH_FORK", "BATCH_PERSISTENT",
 ]
 
 F32, F64_PLAIN = L.TWA_F32, L.TWA_F64_PLAIN
@@ -196,6 +196,10 @@ def twa_set_wait_limit(h, seconds: float) -> None:
 
 def twa_debug_stall_next_batch(h) -> None:
     _check(_lib().twa_debug_stall_next_batch(h), h)
+
+
+def twa_debug_stall_next_tma(h) -> None:
+    _check(_lib().twa_debug_stall_next_tma(h), h)
 
 
 def twa_last_error(h) -> str:

@@ -567,3 +567,36 @@ def test_tma_row_passes_match_cp_async_and_oracle(name, axis_pipeline, tmp_path)
     assert np.array_equal(out[0], out[1])
     ref = oracle_batch(w, cl, w.n_steps)
     assert np.all(field_rel_l2(out[0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
+
+
+def test_a_stalled_tma_tile_times_out_and_the_handle_keeps_working(tmp_path):
+    """Fault injection on the host side of the TMA tile pipeline: the next TMA pass expects 16 bytes
+    per tile that no copy delivers, so every CTA's bounded wait runs out (wait limit 0.05 s), the
+    pass stops and twa_sync_status reports TWA_ETIMEOUT; the GPU keeps answering and the next call
+    (after resampling) matches a handle that never stalled, bitwise."""
+    from paper_2310_07119_gb300 import twa_debug_stall_next_tma, twa_set_wait_limit, twa_sync_status
+    w = ti.small_workload("merger2d", 2, 512, 3, 4, n_tot=1e9, dt=DT_2D)
+    cl = w.psi_cl()
+    path = str(tmp_path / "force_cols.json")
+    _force_columns(w, path, True, True)
+    ens = make_ensemble([w], 0)
+    ens.autotune(path)
+    twa_set_wait_limit(ens.h, 0.05)
+    ens.sample([cl], w.noise_seed)
+    twa_debug_stall_next_tma(ens.h)
+    ens.step(2)
+    assert twa_sync_status(ens.h) == -4                  # TWA_ETIMEOUT
+    assert twa_sync_status(ens.h) == 0                   # the error word was cleared
+    x = torch.ones(1 << 20, device="cuda")
+    assert float(x.sum()) == float(1 << 20)              # the GPU still answers
+    ens.sample([cl], w.noise_seed)
+    ens.step(w.n_steps)
+    assert twa_sync_status(ens.h) == 0
+    got = ens.fields(0).cpu().numpy().copy()
+    ens.close()
+    ref = make_ensemble([w], 0)
+    ref.autotune(path)
+    ref.sample([cl], w.noise_seed)
+    ref.step(w.n_steps)
+    assert np.array_equal(got, ref.fields(0).cpu().numpy())
+    ref.close()
