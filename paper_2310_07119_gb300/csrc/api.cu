@@ -796,10 +796,7 @@ int batch_steps(twa_handle* h, void* psi, int n, double a_first, cudaStream_t st
     for (const auto& I : h->in) nctr += (size_t)I.n_pairs;
     CU(cudaMemsetAsync(h->d_ctr, 0, nctr * sizeof(unsigned), st));
     CU(cudaMemsetAsync(h->d_tick, 0, 2 * sizeof(unsigned long long), st));
-    int dev = 0, khz = 0;
-    CU(cudaGetDevice(&dev));
-    CU(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
-    const long long budget = (long long)(h->wait_limit_s * (double)khz * 1e3);
+    const long long budget = (long long)(h->wait_limit_s * (double)h->clock_khz * 1e3);
     if (launch_batch(T->passes, T->n_passes, T->args, h->d_ctr, h->d_tick, T->n_items, h->d_err,
                      reinterpret_cast<int*>(h->d_tick + 1), budget, T->kinds.data(), (int)T->kinds.size(), st) != 0)
         return fail(h, TWA_ECUDA, "persistent batch launch: cudaFuncSetAttribute failed");

@@ -246,9 +246,14 @@ int tc_gemm(const float* A, long long P, long long K, long long lda, const float
     }
     int ncols = 32;
     while (ncols < Np) ncols <<= 1;
-    int dev = 0, khz = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    // the peak SM clock, queried once: the attribute query costs hundreds of microseconds per call
+    static int khz = 0;
+    if (!khz) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        if (khz <= 0) khz = 2000000;
+    }
     const long long budget = (long long)(wait_s * (double)khz * 1e3);
     const long long ntiles = (P + BM - 1) / BM;
     const int grid = (int)(ntiles < sms ? ntiles : sms);
