@@ -600,3 +600,31 @@ def test_a_stalled_tma_tile_times_out_and_the_handle_keeps_working(tmp_path):
     ref.step(w.n_steps)
     assert np.array_equal(got, ref.fields(0).cpu().numpy())
     ref.close()
+
+
+@pytest.mark.parametrize("n_real", [3, 4])
+def test_sixteen_line_512_columns_match_eight_lines_and_oracle(n_real, tmp_path):
+    """512-point column passes with 16 lines per CTA (512 threads; a warp reads two whole 128-byte
+    rows per access) against the 8-line passes (the same arithmetic per line: bitwise) and the
+    oracle; n_real = 4 leaves a lone last slot."""
+    import json
+    w = ti.small_workload("merger2d", 2, 512, n_real, 10, n_tot=1e9, dt=DT_2D)
+    cl = w.psi_cl()
+    key = f"512x512x1:slots{w.n_real + 1}"
+    out = []
+    for lines in (16, 8):
+        path = str(tmp_path / f"cols{lines}.json")
+        cache = {f"{key}:axis1:op{op}": lines for op in (3, 4, 5, 7)}
+        cache.update({f"{key}:axis0:op{op}": 4 for op in (1, 6, 9)})
+        json.dump(cache, open(path, "w"))
+        ens = make_ensemble([w], 0)
+        ens.autotune(path)
+        chosen = json.load(open(path))
+        assert all(chosen[f"{key}:axis1:op{op}"] == lines for op in (3, 4, 5, 7))
+        ens.sample([cl], w.noise_seed)
+        ens.step(w.n_steps)
+        out.append(ens.fields(0).cpu().numpy().copy())
+        ens.close()
+    assert np.array_equal(out[0], out[1])
+    ref = oracle_batch(w, cl, w.n_steps)
+    assert np.all(field_rel_l2(out[0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
