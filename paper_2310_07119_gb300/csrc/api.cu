@@ -42,7 +42,10 @@ static_assert(OP_COUNT + PL_COUNT == TWA_PROF_NOPS, "profiler op table out of sy
 
 namespace {
 
-constexpr int MODE_1D = 0, MODE_2D = 1, MODE_3D = 2, MODE_3DP = 3;
+// 3D pipelines: MODE_3D axis passes (the Poisson field kept spectral along x between steps), MODE_3DP
+// xy-plane passes for fields and Poisson field, MODE_3DH axis passes for the fields and the xy-plane
+// Poisson pass (the Poisson field real between steps in both)
+constexpr int MODE_1D = 0, MODE_2D = 1, MODE_3D = 2, MODE_3DP = 3, MODE_3DH = 4;
 // Profiler ids of the xy-plane passes follow the line-pass ops.
 constexpr int PROF_PLANE0 = OP_COUNT;
 constexpr int PROF_NOPS = OP_COUNT + PL_COUNT;
@@ -580,6 +583,7 @@ int poisson_init(twa_handle* h, Inst& I, float2* psi, cudaStream_t st) {
             RC(run_pass(h, I, psi, 1, OP_INV, 0.0, I.vc, nullptr, P, st));
             break;
         case MODE_3DP:
+        case MODE_3DH:
             RC(run_pass(h, I, psi, 2, OP_RHO_FWD, 0.0, I.vc, nullptr, P, st));
             RC(run_plane(h, I, psi, PL_POISSON, 0.0, st));
             RC(run_pass(h, I, psi, 2, OP_INV, 0.0, I.vc, nullptr, P, st));
@@ -626,6 +630,14 @@ int steps_f32(twa_handle* h, Inst& I, float2* psi, int n, double a_first, cudaSt
         if (I.prt) RC(particles_step(h, I, psi, k, 1.0, st));
         if (I.mode == MODE_3DP) {
             RC(run_plane(h, I, psi, PL_KICK_DRIFT, k, st));
+            RC(run_pass(h, I, psi, 2, OP_DRIFT_RHO, 0.0, I.vc, nullptr, P, st));
+            RC(run_plane(h, I, psi, PL_POISSON, 0.0, st));
+            RC(run_pass(h, I, psi, 2, OP_INV, 0.0, I.vc, nullptr, P, st));
+        } else if (I.mode == MODE_3DH) {
+            // the fields by axis passes (kick with the real potential, then the x, y and z drifts),
+            // the Poisson field by the xy-plane pass and the z inverse
+            RC(run_pass(h, I, psi, 0, OP_KICK_DRIFT, k, I.vc, nullptr, P, st));
+            RC(run_pass(h, I, psi, 1, OP_DRIFT, 0.0, I.vc, nullptr, I.n_slots, st));
             RC(run_pass(h, I, psi, 2, OP_DRIFT_RHO, 0.0, I.vc, nullptr, P, st));
             RC(run_plane(h, I, psi, PL_POISSON, 0.0, st));
             RC(run_pass(h, I, psi, 2, OP_INV, 0.0, I.vc, nullptr, P, st));
@@ -1950,9 +1962,10 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
                       {1, OP_FWD_MUL_INV, Pn, I.vc, nullptr}, {2, OP_INV, Pn, I.vc, nullptr},
                       {2, OP_RHO_FWD, Pn, I.vc, nullptr}, {0, OP_INV, Pn, I.vc, nullptr},
                       {0, OP_KICK_VINV, Pn, I.vc, nullptr}};
-            if (I.mode == MODE_3DP) {
+            if (I.mode == MODE_3DP || I.mode == MODE_3DH) {
                 passes.push_back({3, PL_KICK_DRIFT, Pn, I.vc, nullptr});
                 passes.push_back({3, PL_POISSON, Pn, I.vc, nullptr});
+                passes.push_back({0, OP_KICK_DRIFT, Pn, I.vc, nullptr});
             }
         }
         if (I.spec) {
@@ -1960,19 +1973,20 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
             for (int ax = 1; ax < I.dim; ++ax) passes.push_back({ax, OP_FWD, Sn, I.spec, nullptr});
         }
         RC(tune_passes(h, I, f, passes, cache, st, e0, e1));
-        if (I.mode == MODE_3DP || I.mode == MODE_3D) {
-            // pick the faster 3D pipeline by timing two whole steps of each
+        if (I.mode == MODE_3DP || I.mode == MODE_3D || I.mode == MODE_3DH) {
+            // pick the fastest 3D pipeline by timing two whole steps of each (cache value 0 axis,
+            // 1 plane, 2 axis passes for the fields with the plane Poisson pass)
             const std::string key = tune_key(I, 9, 0);
             auto hit = cache.find(key);
             const bool eligible = I.n[0] == I.n[1] && I.n[0] >= 16 && I.n[0] <= 256;
+            const int modes[3] = {MODE_3D, MODE_3DP, MODE_3DH};
             if (!eligible) {
                 I.mode = MODE_3D;
-            } else if (hit != cache.end()) {
-                I.mode = hit->second ? MODE_3DP : MODE_3D;
+            } else if (hit != cache.end() && hit->second >= 0 && hit->second <= 2) {
+                I.mode = modes[hit->second];
             } else {
-                float t[2] = {0.f, 0.f};
-                const int modes[2] = {MODE_3D, MODE_3DP};
-                for (int m = 0; m < 2; ++m) {
+                float t[3] = {0.f, 0.f, 0.f};
+                for (int m = 0; m < 3; ++m) {
                     I.mode = modes[m];
                     RC(steps_f32(h, I, f, 1, 1.0, st));
                     CU(cudaEventRecord(e0, st));
@@ -1981,10 +1995,13 @@ extern "C" int twa_autotune(twa_handle* h, void* psi, const char* cache_path, vo
                     CU(cudaEventSynchronize(e1));
                     CU(cudaEventElapsedTime(&t[m], e0, e1));
                 }
-                // the plane pipeline moves fewer bytes but does the same arithmetic; it is taken only
-                // when it is clearly faster (3 %), so near-ties do not flip between runs
-                I.mode = (t[1] < 0.97f * t[0]) ? MODE_3DP : MODE_3D;
-                cache[key] = (I.mode == MODE_3DP) ? 1 : 0;
+                // a pipeline other than the axis one is taken only when it is clearly faster (3 %),
+                // so near-ties do not flip between runs
+                int best = 0;
+                for (int m = 1; m < 3; ++m)
+                    if (t[m] < 0.97f * t[0] && t[m] < (best ? t[best] : t[0])) best = m;
+                I.mode = modes[best];
+                cache[key] = best;
             }
         }
         CU(cudaMemsetAsync(I.vc, 0, (size_t)I.n_pairs * I.cells * sizeof(float2), st));

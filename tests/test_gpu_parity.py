@@ -628,3 +628,32 @@ def test_sixteen_line_512_columns_match_eight_lines_and_oracle(n_real, tmp_path)
     assert np.array_equal(out[0], out[1])
     ref = oracle_batch(w, cl, w.n_steps)
     assert np.all(field_rel_l2(out[0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
+
+
+@pytest.mark.parametrize("n_real", [3, 4])
+def test_hybrid_3d_pipeline_matches_plane_pipeline_and_oracle(n_real, tmp_path):
+    """The hybrid 3D pipeline (axis passes for the fields, the xy-plane pass for the Poisson field,
+    autotune cache value 2) against the plane pipeline (value 1): the same per-line arithmetic, so
+    fields and the moment series of twa_advance are bitwise equal; and the fields against the oracle."""
+    import json
+    from paper_2310_07119_gb300 import twa_advance, twa_sync_status
+    w = ti.small_workload("kgauss", 3, 64, n_real, 20, n_tot=1e8, dt=DT_128)
+    cl = w.psi_cl()
+    key = f"64x64x64:slots{w.n_real + 1}"
+    out = []
+    for pipeline in (2, 1):
+        path = str(tmp_path / f"pipe{pipeline}.json")
+        json.dump({f"{key}:axis9:op0": pipeline}, open(path, "w"))
+        ens = make_ensemble([w], 0)
+        ens.autotune(path)
+        assert json.load(open(path))[f"{key}:axis9:op0"] == pipeline
+        ens.sample([cl], w.noise_seed)
+        series = ens.new_series(w.n_steps, 10)
+        twa_advance(ens.h, ens.psi, w.n_steps, 10, series)
+        assert twa_sync_status(ens.h) == 0
+        out.append((ens.fields(0).cpu().numpy().copy(), series.cpu().numpy().copy()))
+        ens.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    ref = oracle_batch(w, cl, w.n_steps)
+    assert np.all(field_rel_l2(out[0][0].astype(np.complex128), ref, w.grid.dim) < F32_FIELD_TOL)
