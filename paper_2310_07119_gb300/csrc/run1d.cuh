@@ -1,8 +1,8 @@
 // run1d.cuh - a whole 1D run (steps and moment sums of every output) in one launch.
 //
-// A 1D field is one line, so a pair of streams stays in the registers of T threads for the whole
-// run (Sec. III.B.2's split step: kick, drift by FFT / kinetic phase / iFFT, density, Poisson solve
-// by FFT / 1/k^2 / iFFT, all on chip).  At every output the pair's synchronized fields (the pending
+// A 1D field is one line, so each stream stays in the registers of the T threads of its line for
+// the whole run (Sec. III.B.2's split step: kick, drift by FFT / kinetic phase / iFFT, density,
+// Poisson solve by FFT / 1/k^2 / iFFT, all on chip).  At every output the pair's synchronized fields (the pending
 // half kick applied to copies) contribute their per-cell sums |psi|^2, Re psi, Im psi, and the
 // classical slot its |psi_cl|^2, to a partial-sum buffer indexed by (output, pair); one finishing
 // kernel then adds the pairs in pair order and forms the scalars of every output (Eq. E[op],
